@@ -1,0 +1,114 @@
+/*
+ * ldbp.h -- C ABI of the GB300 (sm_103a) split-step / learned-DBP library.
+ *
+ * Method: Haeger & Pfister, "Physics-Based Deep Learning for Fiber-Optic
+ * Communication Systems", arXiv:2010.14258.  Displayed equations are numbered
+ * in order of appearance: Eq. (4) NLSE, (5) time-discretised NLSE,
+ * (6) asymmetric split-step method (SSM), (7) parameterised model,
+ * (8) symmetric SSM, (11) transmit signal, (12) receiver chain,
+ * (14) effective SNR, (15) CD memory.
+ *
+ * Conventions shared by every entry point
+ *  - Complex samples are interleaved complex64 (float re, float im), one
+ *    waveform of n samples per row, rows contiguous: x[b * n + m].  Device
+ *    pointers must be 8-byte aligned; 16-byte alignment enables the TMA
+ *    bulk-copy path (otherwise plain loads are used).
+ *  - Every waveform is periodic (circular): sample index m is taken mod n
+ *    (Sec. IV-A: the symbol sequence is periodic; Sec. III-B: circular
+ *    convolution).
+ *  - The caller owns every device buffer and the stream.  `stream` is a
+ *    cudaStream_t (NULL = legacy default stream).  All work is enqueued
+ *    asynchronously on `stream`; nothing synchronises the device unless stated.
+ *  - Return value: 0 on success, a negative LDBP_E* code otherwise; the
+ *    message of the last failure on the calling thread is ldbp_last_error().
+ *    No call aborts, throws or traps.  Errors detected on the device (a
+ *    bounded wait that ran out) are reported by ldbp_device_status().
+ *  - Gradients follow g = dl/dRe(z) + j dl/dIm(z) for a real loss l.
+ */
+#ifndef LDBP_H_
+#define LDBP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LDBP_OK 0
+#define LDBP_EINVAL (-1)      /* bad size, pointer, length or aliasing */
+#define LDBP_ENOMEM (-2)      /* a library-owned table could not be allocated */
+#define LDBP_ECUDA (-3)       /* a CUDA runtime call failed */
+#define LDBP_ETIMEOUT (-4)    /* a bounded device wait ran out */
+#define LDBP_EUNSUPPORTED (-5) /* valid request outside what this build supports */
+
+/* Largest number of LDBP steps per call and largest filter half-width K
+ * (filter length T = 2K + 1 <= 33) of the fused LDBP kernels. */
+#define LDBP_MAX_STEPS 64
+#define LDBP_MAX_HALF_TAPS 16
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* ldbp_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int ldbp_version(void);
+
+/* Reads and clears the device-side status word of the current device
+ * (synchronises the device).  Returns LDBP_OK, LDBP_ETIMEOUT if a bounded
+ * wait inside a kernel ran out since the last call, or LDBP_ECUDA. */
+int ldbp_device_status(void);
+
+/*
+ * ldbp_apply -- learned digital backpropagation, forward pass.
+ *
+ * Computes y = f_theta(x) of Eq. (7) with the symmetric-FIR linear steps of
+ * Sec. III-B, for each of `batch` waveforms of n samples:
+ *   u_0 = x;  for i = 0..M-1:
+ *     v_m   = sum_{k=-K_i}^{K_i} h^(i)_|k| u_{(m-k) mod n}        (circular FIR)
+ *     u_i+1 = v * exp(j c_i |v|^2)                                 (Kerr step)
+ *   y = u_M.
+ * All M steps run in one fused kernel: each thread block loads a time tile
+ * plus the summed overlap-save halo H = sum_i K_i once (TMA bulk copy), keeps
+ * it on chip for every step and writes its interior once.
+ *
+ *  taps   device, complex64 [M][taps_stride]: half-tap vector
+ *         (h_0, h_1, ..., h_K) of step i at taps[i * taps_stride] (theta of
+ *         Sec. III-B).  Entries beyond K_i are ignored.
+ *  T      host, int32 [M]: filter length T_i = 2 K_i + 1 (odd, 1 <= T_i <= 33,
+ *         T_i <= taps_stride * 2 - 1).  A pruned filter is passed with its
+ *         current (shorter) length.
+ *  c      host, float [M]: nonlinear coefficient of step i (c_i = -gamma
+ *         L_eff(delta_i) for DBP; 0 makes a linear-only layer, Sec. III-C).
+ *  M      number of steps, 1..LDBP_MAX_STEPS.
+ *  x      device, complex64 [batch][n], read only.
+ *  y      device, complex64 [batch][n]; must not overlap x.
+ *  n      samples per waveform (>= 1); batch >= 1.
+ *  ckpt   device, complex64 [M][batch][n], or NULL.  When given, ckpt[i]
+ *         receives u_i (the input of step i); ldbp_backward consumes it.
+ * Errors: LDBP_EINVAL for NULL x/y/taps/T/c, M out of range, an even or
+ * out-of-range T_i, n < 1, batch < 1, overlapping x and y, or a halo sum too
+ * large for one tile (2 H > 2048); LDBP_ECUDA if the launch fails.
+ */
+int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
+               const void* x, void* y, int64_t n, int32_t batch, void* ckpt, void* stream);
+
+/*
+ * ldbp_ubench -- arithmetic ceilings of the current device (synchronous).
+ *
+ * Measures, on every SM, the throughput of one instruction class with eight
+ * independent dependency chains per thread:
+ *   kind 0: scalar FP32 fused multiply-add (lane operations/s),
+ *   kind 1: packed FP32x2 fused multiply-add (lane FP32 operations/s, 2 per lane),
+ *   kind 2: special-function sine (__sinf, operations/s).
+ * These are the denominators the fused kernels' FP32 roofline is checked
+ * against (the paper itself has no hardware figures).  Allocates a 1 KB
+ * scratch buffer and synchronises the device.
+ * Errors: LDBP_EINVAL for a NULL result pointer or an unknown kind; LDBP_ECUDA.
+ */
+int ldbp_ubench(int32_t kind, double* ops_per_second);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDBP_H_ */

@@ -1,0 +1,133 @@
+// C ABI entry points: argument validation, tile planning and kernel dispatch.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "ldbp_fwd.cuh"
+
+namespace ldbp {
+
+__device__ int g_device_status = 0;
+
+static thread_local char t_last_error[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_last_error, sizeof(t_last_error), fmt, ap);
+  va_end(ap);
+}
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(t_last_error, sizeof(t_last_error), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(LDBP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int make_tile_plan(long long n, int H, TilePlan* out) {
+  const int Hp = H + (H & 1);
+  const int Lmax = kFwdS - 2 * Hp;
+  if (2 * H > kFwdS / 2 || Lmax < 2) return -1;
+  long long tpw = (n + Lmax - 1) / Lmax;
+  long long L = (n + tpw - 1) / tpw;
+  L += L & 1;
+  if (L > Lmax) return -1;
+  out->Hp = Hp;
+  out->L = (int)L;
+  out->tiles_per_wave = (int)tpw;
+  return 0;
+}
+
+static bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  const char* pa = static_cast<const char*>(a);
+  const char* pb = static_cast<const char*>(b);
+  return pa < pb + bbytes && pb < pa + abytes;
+}
+
+// Validates taps/lengths/coefficients shared by the forward and adjoint calls.
+static int check_model(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
+                       long long n, int* H, int* kmax) {
+  if (!taps || !T || !c) return fail(LDBP_EINVAL, "taps, T and c must be non-NULL");
+  if (M < 1 || M > LDBP_MAX_STEPS) return fail(LDBP_EINVAL, "M=%d outside 1..%d", M, LDBP_MAX_STEPS);
+  if (taps_stride < 1) return fail(LDBP_EINVAL, "taps_stride=%d < 1", taps_stride);
+  *H = 0;
+  *kmax = 0;
+  for (int i = 0; i < M; ++i) {
+    const int t = T[i];
+    if (t < 1 || (t % 2) == 0) return fail(LDBP_EINVAL, "T[%d]=%d must be odd and >= 1", i, t);
+    const int K = (t - 1) / 2;
+    if (K > LDBP_MAX_HALF_TAPS) return fail(LDBP_EINVAL, "T[%d]=%d exceeds the supported length %d", i, t,
+                                            2 * LDBP_MAX_HALF_TAPS + 1);
+    if (K + 1 > taps_stride) return fail(LDBP_EINVAL, "T[%d]=%d needs taps_stride >= %d", i, t, K + 1);
+    if (!(c[i] == c[i])) return fail(LDBP_EINVAL, "c[%d] is NaN", i);
+    *H += K;
+    *kmax = K > *kmax ? K : *kmax;
+  }
+  (void)n;
+  return 0;
+}
+
+}  // namespace ldbp
+
+using namespace ldbp;
+
+extern "C" {
+
+const char* ldbp_last_error(void) { return t_last_error; }
+
+int ldbp_version(void) { return 100; }
+
+int ldbp_device_status(void) {
+  int h = 0;
+  LDBP_CUDA_TRY(cudaDeviceSynchronize());
+  LDBP_CUDA_TRY(cudaMemcpyFromSymbol(&h, g_device_status, sizeof(int)));
+  const int zero = 0;
+  LDBP_CUDA_TRY(cudaMemcpyToSymbol(g_device_status, &zero, sizeof(int)));
+  if (h == kDevTimeout) return fail(LDBP_ETIMEOUT, "a bounded device wait ran out");
+  if (h != 0) return fail(LDBP_ECUDA, "device status %d", h);
+  return LDBP_OK;
+}
+
+int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M, const void* x,
+               void* y, int64_t n, int32_t batch, void* ckpt, void* stream) {
+  if (!x || !y) return fail(LDBP_EINVAL, "x and y must be non-NULL");
+  if (n < 1 || batch < 1) return fail(LDBP_EINVAL, "n=%lld, batch=%d must be >= 1", (long long)n, batch);
+  int H = 0, kmax = 0;
+  if (int rc = check_model(taps, taps_stride, T, c, M, n, &H, &kmax)) return rc;
+  const size_t bytes = (size_t)n * (size_t)batch * sizeof(float2);
+  if (overlaps(x, bytes, y, bytes)) return fail(LDBP_EINVAL, "x and y overlap");
+  if (ckpt && (overlaps(ckpt, bytes * M, x, bytes) || overlaps(ckpt, bytes * M, y, bytes)))
+    return fail(LDBP_EINVAL, "ckpt overlaps x or y");
+  TilePlan plan;
+  if (make_tile_plan(n, H, &plan)) return fail(LDBP_EINVAL, "halo sum %d too large for one tile", H);
+  if ((long long)plan.tiles_per_wave * batch > 0x7fffffffLL) return fail(LDBP_EINVAL, "grid too large");
+  FwdParams p;
+  memset(&p, 0, sizeof(p));
+  p.x = static_cast<const float2*>(x);
+  p.y = static_cast<float2*>(y);
+  p.ckpt = static_cast<float2*>(ckpt);
+  p.taps = static_cast<const float2*>(taps);
+  p.taps_stride = taps_stride;
+  p.n = n;
+  p.batch = batch;
+  p.M = M;
+  p.tiles_per_wave = plan.tiles_per_wave;
+  p.L = plan.L;
+  p.Hp = plan.Hp;
+  for (int i = 0; i < M; ++i) {
+    p.K[i] = (T[i] - 1) / 2;
+    p.c[i] = c[i];
+  }
+  cudaError_t e = launch_ldbp_fwd(p, kmax, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "ldbp_fwd launch");
+  return LDBP_OK;
+}
+
+}  // extern "C"

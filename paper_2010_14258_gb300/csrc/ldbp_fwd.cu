@@ -1,0 +1,257 @@
+// Fused multi-step learned-DBP forward kernel.
+//
+// Computes Eq. (7) of the paper with the symmetric circular FIR of Sec. III-B
+// as linear step and the Kerr rotation x exp(j c |x|^2) as nonlinear step.
+//
+// Design (GB300):
+//  * One thread block = 256 threads x 16 consecutive samples = a 4096-sample
+//    tile that covers an output interval of L samples plus the summed
+//    overlap-save halo Hp >= sum_i K_i on each side (circular wrap at the
+//    waveform ends).  The tile is read from HBM once with a TMA bulk copy
+//    (cp.async.bulk, completion on an mbarrier) and written back once with a
+//    bulk store: 16 bytes of HBM traffic per sample for all M steps.
+//  * The samples live in registers for all M steps.  Neighbour samples for
+//    the FIR come from the adjacent lanes by warp shuffles; only the two
+//    edge lanes of every warp exchange K samples through shared memory.
+//  * The FIR uses the folded form of Fig. 3: y_m = h_0 x_m + sum_k h_k (x_{m-k} + x_{m+k}).
+//  * The valid window shrinks by K_i per side per step; after M steps the
+//    interior [Hp, Hp + L) of the tile is exact.
+#include <cstdio>
+
+#include "common.cuh"
+#include "ldbp_fwd.cuh"
+
+namespace ldbp {
+
+// Kerr rotation of the thread's samples.  A warp whose phases all lie in
+// [-pi/4, pi/4] (the usual case: the nonlinear phase per step is small)
+// skips the range reduction; results are identical either way.
+__device__ __forceinline__ void kerr_block(float2 (&v)[kFwdR], float c) {
+  float phi[kFwdR];
+  float m = 0.f;
+#pragma unroll
+  for (int r = 0; r < kFwdR; ++r) {
+    phi[r] = c * fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+    m = fmaxf(m, fabsf(phi[r]));
+  }
+  if (__all_sync(0xffffffffu, m <= 0.785398163f)) {
+#pragma unroll
+    for (int r = 0; r < kFwdR; ++r) {
+      const float2 e = expj<false>(phi[r]);
+      v[r] = make_float2(fmaf(v[r].x, e.x, -v[r].y * e.y), fmaf(v[r].x, e.y, v[r].y * e.x));
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kFwdR; ++r) {
+      const float2 e = expj<true>(phi[r]);
+      v[r] = make_float2(fmaf(v[r].x, e.x, -v[r].y * e.y), fmaf(v[r].x, e.y, v[r].y * e.x));
+    }
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void fir_kerr_step(float2 (&v)[kFwdR], const float2* __restrict__ h, float c,
+                                              float2* edge_first, float2* edge_last, int lane, int warp,
+                                              bool compute) {
+  constexpr int E = kFwdR + 2 * K;
+  float2 xe[E];
+  if constexpr (K > 0) {
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) edge_first[warp * kFwdEdge + j] = v[j];
+    }
+    if (lane == 31) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) edge_last[warp * kFwdEdge + j] = v[kFwdR - K + j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      xe[j].x = __shfl_up_sync(0xffffffffu, v[kFwdR - K + j].x, 1);
+      xe[j].y = __shfl_up_sync(0xffffffffu, v[kFwdR - K + j].y, 1);
+      xe[K + kFwdR + j].x = __shfl_down_sync(0xffffffffu, v[j].x, 1);
+      xe[K + kFwdR + j].y = __shfl_down_sync(0xffffffffu, v[j].y, 1);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        xe[j] = warp > 0 ? edge_last[(warp - 1) * kFwdEdge + j] : make_float2(0.f, 0.f);
+    }
+    if (lane == 31) {
+#pragma unroll
+      for (int j = 0; j < K; ++j)
+        xe[K + kFwdR + j] = warp < kFwdNW - 1 ? edge_first[(warp + 1) * kFwdEdge + j] : make_float2(0.f, 0.f);
+    }
+  }
+  if (!compute) return;
+#pragma unroll
+  for (int r = 0; r < kFwdR; ++r) xe[K + r] = v[r];
+  float2 hk[K + 1];
+#pragma unroll
+  for (int k = 0; k <= K; ++k) hk[k] = h[k];
+#pragma unroll
+  for (int r = 0; r < kFwdR; ++r) {
+    const float2 x0 = xe[K + r];
+    float2 acc = make_float2(fmaf(hk[0].x, x0.x, -hk[0].y * x0.y), fmaf(hk[0].x, x0.y, hk[0].y * x0.x));
+#pragma unroll
+    for (int k = 1; k <= K; ++k) acc = cfma(hk[k], cadd(xe[K + r - k], xe[K + r + k]), acc);
+    v[r] = acc;
+  }
+  if (c != 0.f) kerr_block(v, c);
+}
+
+template <int KMAX>
+__device__ __forceinline__ void dispatch_step(int K, float2 (&v)[kFwdR], const float2* h, float c, float2* ef,
+                                              float2* el, int lane, int warp, bool compute) {
+  // Every case is a fully unrolled instance; the branch is uniform per block.
+  switch (K) {
+#define LDBP_CASE(k)                                                    \
+  case k:                                                               \
+    if constexpr (k <= KMAX) fir_kerr_step<k>(v, h, c, ef, el, lane, warp, compute); \
+    break;
+    LDBP_CASE(0) LDBP_CASE(1) LDBP_CASE(2) LDBP_CASE(3) LDBP_CASE(4) LDBP_CASE(5) LDBP_CASE(6)
+    LDBP_CASE(7) LDBP_CASE(8) LDBP_CASE(9) LDBP_CASE(10) LDBP_CASE(11) LDBP_CASE(12) LDBP_CASE(13)
+    LDBP_CASE(14) LDBP_CASE(15) LDBP_CASE(16)
+#undef LDBP_CASE
+    default:
+      break;
+  }
+}
+
+// Loads the S-sample tile starting at circular position g0 of waveform row `src`.
+__device__ __forceinline__ void load_tile(float2* tile, const float2* __restrict__ src, long long n, long long g0,
+                                          uint64_t* bar, bool* timed_out) {
+  const int tid = threadIdx.x;
+  const bool contiguous = g0 >= 0 && g0 + kFwdS <= n;
+  const bool bulk = contiguous && aligned16(src + g0);
+  if (bulk) {
+    if (tid == 0) {
+      mbar_arrive_expect_tx(bar, kFwdS * sizeof(float2));
+      bulk_g2s(tile, src + g0, kFwdS * sizeof(float2), bar);
+    }
+    if (!mbar_wait_bounded(bar, 0)) *timed_out = true;
+  } else {
+    for (int s = tid; s < kFwdS; s += kFwdNT) {
+      long long q = (g0 + s) % n;
+      if (q < 0) q += n;
+      tile[s] = src[q];
+    }
+  }
+}
+
+template <int KMAX, int MINB>
+__global__ void __launch_bounds__(kFwdNT, MINB) ldbp_fwd_kernel(const __grid_constant__ FwdParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2* tile = reinterpret_cast<float2*>(smem_raw);
+  float2* taps_s = tile + kFwdS;                                   // [M][KMAX+1]
+  float2* edges = taps_s + p.M * (KMAX + 1);                       // [2 parity][2][NW][kFwdEdge]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(edges + 4 * kFwdNW * kFwdEdge);
+  __shared__ bool timed_out;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x / p.tiles_per_wave;
+  const int tt = blockIdx.x - b * p.tiles_per_wave;
+  const long long n = p.n;
+  const long long t0 = (long long)tt * p.L;
+  const int Lt = (int)min((long long)p.L, n - t0);
+  if (Lt <= 0) return;  // uniform per block
+  if (*(volatile int*)&g_device_status == kDevTimeout) return;  // an earlier block gave up waiting
+  const float2* src = p.x + (long long)b * n;
+
+  if (tid == 0) {
+    timed_out = false;
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  for (int e = tid; e < p.M * (KMAX + 1); e += kFwdNT) {
+    const int i = e / (KMAX + 1), k = e - i * (KMAX + 1);
+    taps_s[e] = k <= p.K[i] ? p.taps[(long long)i * p.taps_stride + k] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  load_tile(tile, src, n, t0 - p.Hp, bar, &timed_out);
+  __syncthreads();
+  if (timed_out) return;
+
+  float2 v[kFwdR];
+  {
+    const float4* t4 = reinterpret_cast<const float4*>(tile + tid * kFwdR);
+#pragma unroll
+    for (int r = 0; r < kFwdR / 2; ++r) {
+      float4 q = t4[r];
+      v[2 * r] = make_float2(q.x, q.y);
+      v[2 * r + 1] = make_float2(q.z, q.w);
+    }
+  }
+  // Warps entirely beyond the last sample any output depends on skip the arithmetic.
+  const bool compute = warp * 32 * kFwdR < p.L + 2 * p.Hp;
+  const int s0 = tid * kFwdR - p.Hp;  // output offset of v[0]
+
+  int parity = 0;
+  for (int i = 0; i < p.M; ++i) {
+    if (p.ckpt) {
+      float2* dst = p.ckpt + ((long long)i * p.batch + b) * n + t0;
+#pragma unroll
+      for (int r = 0; r < kFwdR; ++r)
+        if (s0 + r >= 0 && s0 + r < Lt) dst[s0 + r] = v[r];
+    }
+    const int K = p.K[i];
+    float2* ef = edges + parity * 2 * kFwdNW * kFwdEdge;
+    float2* el = ef + kFwdNW * kFwdEdge;
+    dispatch_step<KMAX>(K, v, taps_s + i * (KMAX + 1), p.c[i], ef, el, lane, warp, compute);
+    if (K > 0) parity ^= 1;
+  }
+
+  // Stage the result in shared memory and store the interior once.
+  {
+    float4* t4 = reinterpret_cast<float4*>(tile + tid * kFwdR);
+#pragma unroll
+    for (int r = 0; r < kFwdR / 2; ++r) t4[r] = make_float4(v[2 * r].x, v[2 * r].y, v[2 * r + 1].x, v[2 * r + 1].y);
+  }
+  float2* dst = p.y + (long long)b * n + t0;
+  const bool bulk = aligned16(dst) && aligned16(tile + p.Hp) && (Lt % 2 == 0);
+  if (bulk) {
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      bulk_s2g(dst, tile + p.Hp, (uint32_t)Lt * sizeof(float2));
+      bulk_commit();
+      bulk_wait_read0();
+    }
+  } else {
+    __syncthreads();
+    for (int s = tid; s < Lt; s += kFwdNT) dst[s] = tile[p.Hp + s];
+  }
+}
+
+size_t fwd_smem_bytes(int kmax, int M) {
+  return sizeof(float2) * ((size_t)kFwdS + (size_t)M * (kmax + 1) + 4 * kFwdNW * kFwdEdge) + 16;
+}
+
+int fwd_kmax_class(int kmax_needed) {
+  if (kmax_needed <= 2) return 2;
+  if (kmax_needed <= 4) return 4;
+  if (kmax_needed <= 8) return 8;
+  return 16;
+}
+
+template <int KMAX, int MINB>
+static cudaError_t launch_cls(const FwdParams& p, int grid, cudaStream_t st) {
+  const size_t smem = fwd_smem_bytes(KMAX, p.M);
+  cudaError_t e = cudaFuncSetAttribute(ldbp_fwd_kernel<KMAX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  ldbp_fwd_kernel<KMAX, MINB><<<grid, kFwdNT, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ldbp_fwd(const FwdParams& p, int kmax_needed, cudaStream_t st) {
+  const int grid = p.batch * p.tiles_per_wave;
+  switch (fwd_kmax_class(kmax_needed)) {
+    case 2: return launch_cls<2, 2>(p, grid, st);
+    case 4: return launch_cls<4, 2>(p, grid, st);
+    case 8: return launch_cls<8, 2>(p, grid, st);
+    default: return launch_cls<16, 1>(p, grid, st);
+  }
+}
+
+}  // namespace ldbp

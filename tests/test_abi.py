@@ -1,0 +1,54 @@
+"""The C-ABI library builds, loads and exports every declared symbol; host-side
+argument checks return error codes without touching a GPU."""
+import ctypes
+
+import pytest
+
+from paper_2010_14258_gb300 import _lib, build
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return _lib.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = _lib.declared_symbols()
+    assert "ldbp_apply" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_version(L):
+    assert L.ldbp_version() >= 100
+
+
+def _apply(L, **kw):
+    args = dict(taps=ctypes.c_void_p(16), stride=2, T=[3], c=[-0.1], M=1, x=ctypes.c_void_p(4096),
+                y=ctypes.c_void_p(1 << 20), n=128, B=1, ckpt=None)
+    args.update(kw)
+    return L.ldbp_apply(args["taps"], args["stride"], _lib.i32_array(args["T"]) if args["T"] is not None else None,
+                        _lib.f32_array(args["c"]) if args["c"] is not None else None, args["M"], args["x"],
+                        args["y"], args["n"], args["B"], args["ckpt"], None)
+
+
+@pytest.mark.parametrize("kw, needle", [
+    (dict(x=None), "non-NULL"),
+    (dict(taps=None), "non-NULL"),
+    (dict(T=[4]), "odd"),
+    (dict(T=[0]), "odd"),
+    (dict(T=[35], stride=20), "supported length"),
+    (dict(T=[7], stride=2), "taps_stride"),
+    (dict(M=0, T=[3]), "M=0"),
+    (dict(M=65, T=[3] * 65, c=[0.0] * 65), "M=65"),
+    (dict(n=0), "n=0"),
+    (dict(B=0), "batch=0"),
+    (dict(y=ctypes.c_void_p(4096 + 8)), "overlap"),
+    (dict(c=[float("nan")]), "NaN"),
+    (dict(ckpt=ctypes.c_void_p(4096 + 512)), "ckpt overlaps"),
+])
+def test_ldbp_apply_rejects(L, kw, needle):
+    rc = _apply(L, **kw)
+    assert rc == -1
+    assert needle in L.ldbp_last_error().decode()

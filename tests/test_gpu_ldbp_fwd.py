@@ -1,0 +1,132 @@
+"""Parity of the fused LDBP forward kernel (CUDA, FP32) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ldbp as oldbp
+from oracle import nlse, txrx
+from tests.util import c64, gpu_lib, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _model(Ts, seed, ls=True, fs=20e9, span_km=80.0):
+    """Gain-capped LS taps of one span's dispersion (plus a 1 % perturbation),
+    c = -gamma L_eff(span).  The gain cap keeps the 25-step cascade well
+    conditioned, so FP32 and FP64 results stay comparable."""
+    from paper_2010_14258_gb300 import init
+    base, cs = init.ldbp_init(Ts, span_km=span_km, fs=fs)
+    taps = []
+    for i, (T, h) in enumerate(zip(Ts, base)):
+        if not ls:
+            h = np.eye(1, (T - 1) // 2 + 1)[0].astype(complex)
+        h = h + synth.complex_normal(len(h), seed + i, 0.01 * abs(h[0]))
+        taps.append(c64(h))
+    return taps, [float(np.float32(ci)) for ci in cs]
+
+
+def _signal(B, n, seed, pw):
+    """Band-limited 16-QAM RRC waveform (2 samples/symbol) of mean power pw, n even;
+    odd n uses white Gaussian samples instead."""
+    if n % 2:
+        return c64(synth.gaussian_waveform(B, n, seed, pw))
+    s = synth.qam16_symbols(B, n // 2, seed)
+    return c64(txrx.tx(s, 2, 0.1, pw))
+
+
+def _pack(taps, stride=None):
+    stride = stride or max(len(h) for h in taps)
+    arr = np.zeros((len(taps), stride), np.complex128)
+    for i, h in enumerate(taps):
+        arr[i, : len(h)] = h
+    return arr
+
+
+def _run(taps, Ts, c, x, ckpt=False):
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    td = to_dev(_pack(taps))
+    xd = to_dev(x)
+    ck = torch.empty((len(Ts),) + tuple(xd.shape), dtype=torch.complex64, device="cuda") if ckpt else None
+    y = api.ldbp_apply(td, Ts, c, xd, ckpt=ck)
+    torch.cuda.synchronize()
+    return to_np(y), (to_np(ck) if ckpt else None)
+
+
+CASES = [
+    # (Ts, B, n, power_w)
+    ([3] * 25, 3, 10000, 5e-3),          # several tiles + ragged tail
+    ([5] * 25, 2, 12290, 5e-3),
+    ([9] * 25, 2, 9001, 2e-3),           # odd n: unaligned rows, plain-load path
+    ([15] * 25, 2, 16384, 2e-3),
+    ([31, 15, 9, 3] * 2, 2, 8192, 2e-3),
+    ([5, 3] * 12 + [5], 2, 8000, 4e-3),  # alternating lengths after pruning
+    ([33] * 4, 1, 6000, 2e-3),           # longest supported filter
+    ([1, 3, 1, 5], 2, 4096, 1e-2),       # T = 1 steps
+]
+
+
+@pytest.mark.parametrize("Ts,B,n,pw", CASES)
+def test_ldbp_forward_parity(Ts, B, n, pw):
+    taps, c = _model(Ts, seed=len(Ts) * 7 + n)
+    x = _signal(B, n, n, pw)
+    y, _ = _run(taps, Ts, c, x)
+    ref, _ = oldbp.forward(x, taps, c)
+    assert rel_l2(y, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 511, 4096, 4097])
+def test_ldbp_forward_short_waveforms_wrap(n):
+    # waveforms shorter than a tile wrap around several times (circular index)
+    Ts = [5, 9, 3]
+    taps, c = _model(Ts, seed=n)
+    x = c64(synth.gaussian_waveform(3, n, 100 + n, 5e-3))
+    y, _ = _run(taps, Ts, c, x)
+    ref, _ = oldbp.forward(x, taps, c)
+    assert rel_l2(y, ref) <= 1e-5 * len(Ts)
+
+
+def test_ldbp_single_step_error_and_checkpoints():
+    Ts = [9] * 25
+    taps, c = _model(Ts, seed=3)
+    x = _signal(2, 20000, 5, 5e-3)
+    y, ck = _run(taps, Ts, c, x, ckpt=True)
+    ref, inputs = oldbp.forward(x, taps, c)
+    assert rel_l2(y, ref) <= 1e-4
+    for i in range(len(Ts)):
+        # checkpoint i is the input of step i
+        assert rel_l2(ck[i], inputs[i]) <= 1e-4
+        # one step applied to the oracle's own input: error <= 1e-5 per step
+        yi, _ = _run([taps[i]], [Ts[i]], [c[i]], c64(inputs[i]))
+        ri, _ = oldbp.forward(c64(inputs[i]), [taps[i]], [c[i]])
+        assert rel_l2(yi, ri) <= 1e-5
+
+
+def test_linear_only_layers_and_large_phase():
+    # c = 0 layers are pure FIR; a large Kerr phase (up to ~1 rad) stays accurate
+    Ts = [7, 7, 7]
+    taps, _ = _model(Ts, seed=9, ls=False)
+    x = c64(synth.gaussian_waveform(2, 5000, 9, 1.0))
+    for c in ([0.0, 0.0, 0.0], [-0.3, 0.25, 0.0]):
+        y, _ = _run(taps, Ts, c, x)
+        ref, _ = oldbp.forward(x, taps, c)
+        assert rel_l2(y, ref) <= 1e-5 * 10
+
+
+def test_full_size_sampled():
+    # 256 x 65536 at M = 25, T = 3: compare sampled waveforms, full length
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    Ts = [3] * 25
+    taps, c = _model(Ts, seed=2)
+    B, n = 256, 65536
+    g = torch.Generator(device="cuda").manual_seed(0)
+    xd = (torch.randn(B, n, generator=g, device="cuda", dtype=torch.complex64) * (2e-3 ** 0.5))
+    y = api.ldbp_apply(to_dev(_pack(taps)), Ts, c, xd)
+    torch.cuda.synchronize()
+    for b in (0, 77, 255):
+        xb = to_np(xd[b])
+        ref, _ = oldbp.forward(xb, taps, c)
+        assert rel_l2(to_np(y[b]), ref) <= 1e-4
