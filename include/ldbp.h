@@ -92,6 +92,74 @@ int ldbp_device_status(void);
 int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
                const void* x, void* y, int64_t n, int32_t batch, void* ckpt, void* stream);
 
+/* Fiber parameters in the paper's units (Table I). */
+typedef struct {
+  double alpha_db_per_km;   /* power attenuation, dB/km (>= 0) */
+  double beta2_ps2_per_km;  /* group-velocity dispersion, ps^2/km */
+  double gamma_per_w_km;    /* Kerr nonlinearity, 1/(W km) */
+} ldbp_fiber;
+
+/* Link (Sec. IV-A): n_spans spans of span_km, each followed by an EDFA that
+ * restores the launch power and (if ase != 0) adds white Gaussian ASE noise of
+ * PSD (e^{alpha L_sp} - 1) h nu_s n_sp, n_sp = NF / (2 (1 - e^{-alpha L_sp})).
+ * steps_per_span uniform split steps of delta = span_km / steps_per_span;
+ * symmetric != 0 selects Eq. (8), otherwise Eq. (6).  The ASE realisation is
+ * drawn by Philox4x32-10 with key (seed lo, seed hi) and counter words
+ * (bin k / 2, waveform, span, counter lo) in the frequency domain. */
+typedef struct {
+  int32_t n_spans;
+  double span_km;
+  int32_t steps_per_span;
+  int32_t symmetric;
+  int32_t ase;
+  double nf_db;
+  double carrier_hz;
+  uint64_t seed;
+  uint64_t counter;
+} ldbp_link;
+
+/*
+ * ssm_forward -- fiber channel by the split-step Fourier method.
+ *
+ * Propagates each waveform over the link: per span, steps_per_span steps of
+ * the symmetric SSM (Eq. (8): A_{d/2} sigma_d A_{d/2}, with the Kerr rotation
+ * x exp(j gamma l(d) |x|^2), l(d) = 2 sinh(alpha d / 2) / alpha, at the step
+ * midpoint) or of the asymmetric SSM (Eq. (6), Kerr with L_eff(d) first, then
+ * the lossy linear step A_d = e^{-alpha d/2} F^-1 diag(exp(j beta2/2 w_k^2 d)) F),
+ * then the amplifier gain e^{alpha L_sp / 2} and the ASE noise.
+ * omega_k = 2 pi fs kappa_k / n with kappa_k the fftfreq integers (Eq. (5)).
+ *
+ *  fiber, link   host structs (read during the call only).
+ *  fs_hz         sampling rate of the waveform.
+ *  x             device complex64 [batch][n] launch waveform in sqrt(W).
+ *  y             device complex64 [batch][n]; may equal x (in place).
+ *  n             power of two, 512 <= n <= 262144.
+ * One kernel launch runs all steps; each waveform stays in the shared memory
+ * of a thread-block cluster.  The first call for a given (device, fiber,
+ * link, fs, n) computes the FP64 spectral tables and uploads them into
+ * library-owned device memory (cudaMalloc + synchronous copy); later calls
+ * reuse them.
+ * Errors: LDBP_EINVAL (NULL pointer, n not a supported power of two,
+ * non-positive fs/span/steps/batch, negative alpha); LDBP_ECUDA.
+ */
+int ssm_forward(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, const void* x, void* y, int64_t n,
+                int32_t batch, void* stream);
+
+/*
+ * dbp_apply -- full-length frequency-domain digital backpropagation.
+ *
+ * Solves the propagation backwards (Sec. IV): spans in reverse order, the
+ * amplifier gain undone, and steps_per_span steps of the SSM with
+ * (beta2, gamma, alpha) -> (-beta2, -gamma, -alpha): symmetric != 0 gives
+ * A^-1_{d/2} sigma_{-d} A^-1_{d/2} (the exact inverse of the symmetric
+ * channel step), otherwise Eq. (6) order: linear step with full-length
+ * dispersion filter, then Kerr rotation with -gamma L_eff(d).
+ * link->ase, seed and counter are ignored.  Arguments and errors as
+ * ssm_forward; y may equal x.
+ */
+int dbp_apply(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, int32_t steps_per_span,
+              int32_t symmetric, const void* x, void* y, int64_t n, int32_t batch, void* stream);
+
 /*
  * ldbp_ubench -- arithmetic ceilings of the current device (synchronous).
  *

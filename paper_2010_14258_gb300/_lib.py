@@ -36,6 +36,10 @@ _SIGNATURES = {
     "ldbp_last_error": (ctypes.c_char_p, []),
     "ldbp_version": (c_int, []),
     "ldbp_device_status": (c_int, []),
+    "ssm_forward": (c_int, [ctypes.POINTER(LdbpFiber), ctypes.POINTER(LdbpLink), c_double, c_void_p, c_void_p,
+                            c_int64, c_int32, c_void_p]),
+    "dbp_apply": (c_int, [ctypes.POINTER(LdbpFiber), ctypes.POINTER(LdbpLink), c_double, c_int32, c_int32,
+                          c_void_p, c_void_p, c_int64, c_int32, c_void_p]),
     "ldbp_ubench": (c_int, [c_int32, ctypes.POINTER(c_double)]),
     "ldbp_apply": (c_int, [c_void_p, c_int32, P_int32, P_float, c_int32, c_void_p, c_void_p, c_int64, c_int32,
                            c_void_p, c_void_p]),

@@ -59,3 +59,43 @@ def ubench(kind: int) -> float:
     out = ctypes.c_double(0.0)
     _lib.check(_lib.lib().ldbp_ubench(kind, ctypes.byref(out)))
     return out.value
+
+
+def fiber_struct(fiber):
+    """ldbp_fiber from an object with alpha_db_per_km, beta2_ps2_per_km, gamma_per_w_km."""
+    return _lib.LdbpFiber(float(fiber.alpha_db_per_km), float(fiber.beta2_ps2_per_km), float(fiber.gamma_per_w_km))
+
+
+def link_struct(link):
+    return _lib.LdbpLink(int(link.n_spans), float(link.span_km), int(link.steps_per_span), int(bool(link.symmetric)),
+                         int(bool(link.ase)), float(link.nf_db), float(link.carrier_hz), int(link.seed) & (2**64 - 1),
+                         int(link.counter) & (2**64 - 1))
+
+
+def _batched(x):
+    squeeze = x.dim() == 1
+    x2 = x.unsqueeze(0) if squeeze else x
+    _check_c64("x", x2)
+    return x2, squeeze
+
+
+def ssm_forward(fiber, link, fs, x, out=None):
+    """Split-step channel (Eqs. (6)/(8), Sec. IV-A).  x: complex64 [B, n] or [n] (n a power of two)."""
+    import ctypes
+    x2, squeeze = _batched(x)
+    y = torch.empty_like(x2) if out is None else out
+    f, l = fiber_struct(fiber), link_struct(link)
+    _lib.check(_lib.lib().ssm_forward(ctypes.byref(f), ctypes.byref(l), float(fs), _ptr(x2), _ptr(y), x2.shape[1],
+                                      x2.shape[0], _stream()))
+    return y[0] if squeeze else y
+
+
+def dbp_apply(fiber, link, fs, x, steps_per_span=1, symmetric=False, out=None):
+    """Full-length frequency-domain DBP (the SSM run backwards)."""
+    import ctypes
+    x2, squeeze = _batched(x)
+    y = torch.empty_like(x2) if out is None else out
+    f, l = fiber_struct(fiber), link_struct(link)
+    _lib.check(_lib.lib().dbp_apply(ctypes.byref(f), ctypes.byref(l), float(fs), int(steps_per_span),
+                                    int(bool(symmetric)), _ptr(x2), _ptr(y), x2.shape[1], x2.shape[0], _stream()))
+    return y[0] if squeeze else y

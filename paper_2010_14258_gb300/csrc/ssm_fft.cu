@@ -1,0 +1,45 @@
+// Dispatch of the cluster-resident split-step kernel over (N2, P) and the
+// choice of the cluster size.  The kernel instances live in ssm_p*.cu so that
+// they compile in parallel.
+#include "common.cuh"
+#include "ssm.cuh"
+
+namespace ldbp {
+
+template <int LOGN2, int P>
+cudaError_t launch_one(const SsmParams& p, cudaStream_t st);
+
+#define LDBP_SSM_CASES(L)                          \
+  case 1: return launch_one<L, 1>(p, st);          \
+  case 2: return launch_one<L, 2>(p, st);          \
+  case 4: return launch_one<L, 4>(p, st);          \
+  case 8: return launch_one<L, 8>(p, st);          \
+  case 16: return launch_one<L, 16>(p, st);        \
+  default: return cudaErrorInvalidValue;
+
+cudaError_t launch_ssm(const SsmParams& p, int P, int log_n2, cudaStream_t st) {
+  switch (log_n2) {
+    case 9: return P == 1 ? launch_one<9, 1>(p, st) : cudaErrorInvalidValue;
+    case 10: return P == 1 ? launch_one<10, 1>(p, st) : cudaErrorInvalidValue;
+    case 11: switch (P) { LDBP_SSM_CASES(11) }
+    case 12: switch (P) { LDBP_SSM_CASES(12) }
+    case 13: switch (P) { LDBP_SSM_CASES(13) }
+    case 14: switch (P) { LDBP_SSM_CASES(14) }
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int ssm_choose_cluster(long long n, int batch, int sm_count, int* P, int* log_n2) {
+  int logn = 0;
+  while ((1LL << logn) < n) ++logn;
+  if ((1LL << logn) != n || logn < kSsmMinLogN2 || logn > kSsmMaxLogN2 + 4) return -1;
+  int p = 1;
+  while (logn - __builtin_ctz(p) > kSsmMaxLogN2) p *= 2;
+  // more blocks per waveform while the batch alone does not fill the GPU
+  while (p < 16 && logn - __builtin_ctz(p) - 1 >= 11 && (long long)batch * p < sm_count) p *= 2;
+  *P = p;
+  *log_n2 = logn - __builtin_ctz(p);
+  return 0;
+}
+
+}  // namespace ldbp

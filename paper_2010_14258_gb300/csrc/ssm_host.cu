@@ -1,0 +1,284 @@
+// Host side of the split-step path: FP64 construction of the per-step spectral
+// tables of the channel and of DBP, a per-device cache of those tables, and
+// the C ABI entry points ssm_forward / dbp_apply.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "ssm.cuh"
+#include "ssm_host.cuh"
+
+namespace ldbp {
+
+static const double kPi = 3.14159265358979323846;
+static const double kPlanck = 6.626e-34;  // Table I
+
+FiberSI to_si(const ldbp_fiber& f) {
+  FiberSI s;
+  s.alpha = f.alpha_db_per_km * std::log(10.0) / 10.0 / 1e3;
+  s.beta2 = f.beta2_ps2_per_km * 1e-27;
+  s.gamma = f.gamma_per_w_km * 1e-3;
+  return s;
+}
+
+double leff(double alpha, double z) { return alpha == 0.0 ? z : -std::expm1(-alpha * z) / alpha; }
+double lmid(double alpha, double z) { return alpha == 0.0 ? z : 2.0 * std::sinh(alpha * z / 2.0) / alpha; }
+
+// exp(j (beta2/2) w_k^2 z) e^{-alpha z / 2} / n on the fftfreq grid (Eq. (5)).
+static std::vector<std::complex<double>> dispersion_table(long long n, double fs, double beta2, double alpha,
+                                                          double z) {
+  std::vector<std::complex<double>> t((size_t)n);
+  const double amp = std::exp(-alpha * z / 2.0) / (double)n;
+  for (long long k = 0; k < n; ++k) {
+    const double kk = (double)(k < (n + 1) / 2 ? k : k - n);
+    const double w = 2.0 * kPi * fs * kk / (double)n;
+    const double ph = beta2 / 2.0 * w * w * z;
+    t[(size_t)k] = std::polar(amp, ph);
+  }
+  return t;
+}
+
+SsmProgram build_channel(const ldbp_fiber& f, const ldbp_link& l, double fs, long long n) {
+  const FiberSI s = to_si(f);
+  const double Lsp = l.span_km * 1e3;
+  const int N = l.steps_per_span;
+  const double d = Lsp / N;
+  const double G = std::exp(s.alpha * Lsp / 2.0);
+  SsmProgram p;
+  if (l.ase) {
+    const double nf = std::pow(10.0, l.nf_db / 10.0);
+    const double g = std::exp(s.alpha * Lsp);
+    const double nsp = nf / (2.0 * (1.0 - 1.0 / g));
+    const double psd = (g - 1.0) * kPlanck * l.carrier_hz * nsp;
+    p.noise_std = std::sqrt((double)n * psd * fs / 2.0);
+  }
+  const int16_t no_noise = -2;
+  if (l.symmetric) {
+    p.tabs.push_back(dispersion_table(n, fs, s.beta2, s.alpha, d / 2.0));  // 0: half step
+    p.tabs.push_back(dispersion_table(n, fs, s.beta2, s.alpha, d));        // 1: full step
+    const float c = (float)(s.gamma * lmid(s.alpha, d));
+    p.steps.push_back({0, no_noise, 0, 1.0f, c});
+    for (int sp = 0; sp < l.n_spans; ++sp)
+      for (int i = 0; i < N; ++i) {
+        if (sp == 0 && i == 0) continue;
+        if (i == 0)  // span boundary: half step, amplifier (+ ASE), half step
+          p.steps.push_back({1, (int16_t)(l.ase ? 0 : no_noise), sp - 1, (float)G, c});
+        else
+          p.steps.push_back({1, no_noise, 0, 1.0f, c});
+      }
+    p.steps.push_back({0, (int16_t)(l.ase ? -1 : no_noise), l.n_spans - 1, (float)G, 0.0f});
+  } else {
+    p.tabs.push_back(dispersion_table(n, fs, s.beta2, s.alpha, d));  // 0: full step
+    const float c = (float)(s.gamma * leff(s.alpha, d));
+    p.c_pre = c;
+    const int total = l.n_spans * N;
+    for (int g = 0; g < total; ++g) {
+      const bool end = (g + 1) % N == 0;
+      p.steps.push_back({0, (int16_t)(end && l.ase ? -1 : no_noise), g / N, end ? (float)G : 1.0f,
+                         g == total - 1 ? 0.0f : c});
+    }
+  }
+  return p;
+}
+
+SsmProgram build_dbp(const ldbp_fiber& f, const ldbp_link& l, double fs, long long n, int N, bool symmetric) {
+  const FiberSI s = to_si(f);
+  const double Lsp = l.span_km * 1e3;
+  const double d = Lsp / N;
+  const double Ginv = std::exp(-s.alpha * Lsp / 2.0);
+  SsmProgram p;
+  const int16_t no_noise = -2;
+  if (symmetric) {
+    p.tabs.push_back(dispersion_table(n, fs, -s.beta2, -s.alpha, d / 2.0));
+    p.tabs.push_back(dispersion_table(n, fs, -s.beta2, -s.alpha, d));
+    const float c = (float)(-s.gamma * lmid(s.alpha, d));
+    p.steps.push_back({0, no_noise, 0, (float)Ginv, c});
+    for (int sp = 0; sp < l.n_spans; ++sp)
+      for (int i = 0; i < N; ++i) {
+        if (sp == 0 && i == 0) continue;
+        p.steps.push_back({1, no_noise, 0, i == 0 ? (float)Ginv : 1.0f, c});
+      }
+    p.steps.push_back({0, no_noise, 0, 1.0f, 0.0f});
+  } else {
+    p.tabs.push_back(dispersion_table(n, fs, -s.beta2, -s.alpha, d));
+    const float c = (float)(-s.gamma * leff(s.alpha, d));
+    const int total = l.n_spans * N;
+    for (int g = 0; g < total; ++g) p.steps.push_back({0, no_noise, 0, g % N == 0 ? (float)Ginv : 1.0f, c});
+  }
+  return p;
+}
+
+// ---------------------------------------------------------------- device cache
+static std::mutex g_cache_mu;
+static std::map<std::string, std::shared_ptr<DeviceProgram>> g_programs;
+static std::map<std::string, float2*> g_twiddles;
+
+static cudaError_t upload_c64(const std::vector<std::complex<double>>& v, float2** out) {
+  std::vector<float2> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = make_float2((float)v[i].real(), (float)v[i].imag());
+  cudaError_t e = cudaMalloc(out, h.size() * sizeof(float2));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*out, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
+}
+
+int get_twiddle(long long n, float2** out) {
+  int dev = 0;
+  LDBP_CUDA_TRY(cudaGetDevice(&dev));
+  const std::string key = std::to_string(dev) + ":" + std::to_string(n);
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_twiddles.find(key);
+  if (it != g_twiddles.end()) {
+    *out = it->second;
+    return 0;
+  }
+  std::vector<std::complex<double>> w((size_t)n);
+  for (long long t = 0; t < n; ++t) w[(size_t)t] = std::polar(1.0, -2.0 * kPi * (double)t / (double)n);
+  float2* d = nullptr;
+  cudaError_t e = upload_c64(w, &d);
+  if (e != cudaSuccess) return cuda_fail(e, "twiddle table");
+  g_twiddles[key] = d;
+  *out = d;
+  return 0;
+}
+
+int get_program(const std::string& key_in, const SsmProgram& prog, std::shared_ptr<DeviceProgram>* out) {
+  int dev = 0;
+  LDBP_CUDA_TRY(cudaGetDevice(&dev));
+  const std::string key = std::to_string(dev) + "|" + key_in;
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  auto it = g_programs.find(key);
+  if (it != g_programs.end()) {
+    *out = it->second;
+    return 0;
+  }
+  auto dp = std::make_shared<DeviceProgram>();
+  for (const auto& t : prog.tabs) {
+    float2* d = nullptr;
+    cudaError_t e = upload_c64(t, &d);
+    if (e != cudaSuccess) return cuda_fail(e, "ssm table");
+    dp->tabs.push_back(d);
+  }
+  cudaError_t e = cudaMalloc(&dp->steps, prog.steps.size() * sizeof(SsmStep));
+  if (e != cudaSuccess) return cuda_fail(e, "ssm steps");
+  e = cudaMemcpy(dp->steps, prog.steps.data(), prog.steps.size() * sizeof(SsmStep), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "ssm steps copy");
+  dp->nsteps = (int)prog.steps.size();
+  dp->c_pre = (float)prog.c_pre;
+  dp->noise_std = (float)prog.noise_std;
+  g_programs[key] = dp;
+  *out = dp;
+  return 0;
+}
+
+static std::string fkey(const ldbp_fiber& f, double fs, long long n) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%.17g,%.17g,%.17g,%.17g,%lld", f.alpha_db_per_km, f.beta2_ps2_per_km,
+           f.gamma_per_w_km, fs, n);
+  return buf;
+}
+
+static int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x, const void* y, long long n,
+                      int batch) {
+  if (!f || !l || !x || !y) return fail(LDBP_EINVAL, "fiber, link, x and y must be non-NULL");
+  if (!(fs > 0.0) || !std::isfinite(fs)) return fail(LDBP_EINVAL, "fs_hz must be positive");
+  if (!std::isfinite(f->alpha_db_per_km) || !std::isfinite(f->beta2_ps2_per_km) || !std::isfinite(f->gamma_per_w_km) ||
+      f->alpha_db_per_km < 0)
+    return fail(LDBP_EINVAL, "fiber parameters must be finite (alpha >= 0)");
+  if (l->n_spans < 1 || !(l->span_km > 0.0) || l->steps_per_span < 1)
+    return fail(LDBP_EINVAL, "link needs n_spans >= 1, span_km > 0, steps_per_span >= 1");
+  if (batch < 1) return fail(LDBP_EINVAL, "batch=%d must be >= 1", batch);
+  if (n < (1LL << kSsmMinLogN2) || n > (1LL << (kSsmMaxLogN2 + 4)) || (n & (n - 1)))
+    return fail(LDBP_EINVAL, "n=%lld must be a power of two in [%d, %d]", n, 1 << kSsmMinLogN2,
+                1 << (kSsmMaxLogN2 + 4));
+  if ((long long)l->n_spans * l->steps_per_span > 1000000) return fail(LDBP_EINVAL, "too many steps");
+  return 0;
+}
+
+int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, const float* wave_scale,
+                uint64_t seed, uint64_t counter, cudaStream_t st) {
+  int sms = 0, dev = 0;
+  LDBP_CUDA_TRY(cudaGetDevice(&dev));
+  LDBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int P = 1, log_n2 = 0;
+  if (ssm_choose_cluster(n, batch, sms, &P, &log_n2)) return fail(LDBP_EINVAL, "unsupported n=%lld", n);
+  float2* tw = nullptr;
+  if (int rc = get_twiddle(n, &tw)) return rc;
+  SsmParams p;
+  memset(&p, 0, sizeof(p));
+  p.x = static_cast<const float2*>(x);
+  p.y = static_cast<float2*>(y);
+  p.n = n;
+  p.batch = batch;
+  p.nsteps = dp.nsteps;
+  p.steps = dp.steps;
+  for (size_t i = 0; i < dp.tabs.size() && i < (size_t)kSsmMaxTabs; ++i) p.tabs[i] = dp.tabs[i];
+  p.twiddle = tw;
+  p.wave_scale = wave_scale;
+  p.c_pre = dp.c_pre;
+  p.noise_std = dp.noise_std;
+  p.seed_lo = (uint32_t)(seed & 0xffffffffu);
+  p.seed_hi = (uint32_t)(seed >> 32);
+  p.counter = (uint32_t)(counter & 0xffffffffu);
+  cudaError_t e = launch_ssm(p, P, log_n2, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ssm launch");
+  return 0;
+}
+
+}  // namespace ldbp
+
+using namespace ldbp;
+
+extern "C" {
+
+int ssm_forward(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, const void* x, void* y, int64_t n,
+                int32_t batch, void* stream) {
+  if (int rc = check_link(fiber, link, fs_hz, x, y, n, batch)) return rc;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "ch|%d,%.17g,%d,%d,%d,%.17g,%.17g", link->n_spans, link->span_km,
+           link->steps_per_span, link->symmetric, link->ase, link->nf_db, link->carrier_hz);
+  const std::string key = fkey(*fiber, fs_hz, n) + buf;
+  std::shared_ptr<DeviceProgram> dp;
+  {
+    // building the FP64 tables only on a cache miss
+    int dev = 0;
+    LDBP_CUDA_TRY(cudaGetDevice(&dev));
+    SsmProgram prog;
+    bool need = true;
+    {
+      std::lock_guard<std::mutex> lk(g_cache_mu);
+      need = g_programs.find(std::to_string(dev) + "|" + key) == g_programs.end();
+    }
+    if (need) prog = build_channel(*fiber, *link, fs_hz, n);
+    if (int rc = get_program(key, prog, &dp)) return rc;
+  }
+  return run_program(*dp, x, y, n, batch, nullptr, link->seed, link->counter, static_cast<cudaStream_t>(stream));
+}
+
+int dbp_apply(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, int32_t steps_per_span,
+              int32_t symmetric, const void* x, void* y, int64_t n, int32_t batch, void* stream) {
+  if (int rc = check_link(fiber, link, fs_hz, x, y, n, batch)) return rc;
+  if (steps_per_span < 1) return fail(LDBP_EINVAL, "steps_per_span=%d must be >= 1", steps_per_span);
+  char buf[256];
+  snprintf(buf, sizeof(buf), "dbp|%d,%.17g,%d,%d", link->n_spans, link->span_km, steps_per_span, symmetric ? 1 : 0);
+  const std::string key = fkey(*fiber, fs_hz, n) + buf;
+  std::shared_ptr<DeviceProgram> dp;
+  int dev = 0;
+  LDBP_CUDA_TRY(cudaGetDevice(&dev));
+  SsmProgram prog;
+  bool need = true;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    need = g_programs.find(std::to_string(dev) + "|" + key) == g_programs.end();
+  }
+  if (need) prog = build_dbp(*fiber, *link, fs_hz, n, steps_per_span, symmetric != 0);
+  if (int rc = get_program(key, prog, &dp)) return rc;
+  return run_program(*dp, x, y, n, batch, nullptr, 0, 0, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

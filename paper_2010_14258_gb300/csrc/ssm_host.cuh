@@ -1,0 +1,45 @@
+// Host-side split-step programs (FP64 tables) and their per-device cache.
+#pragma once
+
+#include <complex>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ldbp.h"
+#include "ssm.cuh"
+
+namespace ldbp {
+
+struct FiberSI {
+  double alpha, beta2, gamma;  // 1/m (power), s^2/m, 1/(W m)
+};
+FiberSI to_si(const ldbp_fiber& f);
+double leff(double alpha, double z);
+double lmid(double alpha, double z);
+
+// Spectral tables (DFT order, 1/n folded in) and steps of one split-step run.
+struct SsmProgram {
+  std::vector<std::vector<std::complex<double>>> tabs;
+  std::vector<SsmStep> steps;
+  double c_pre = 0.0;
+  double noise_std = 0.0;
+};
+
+SsmProgram build_channel(const ldbp_fiber& f, const ldbp_link& l, double fs, long long n);
+SsmProgram build_dbp(const ldbp_fiber& f, const ldbp_link& l, double fs, long long n, int steps_per_span,
+                     bool symmetric);
+
+struct DeviceProgram {
+  std::vector<float2*> tabs;
+  SsmStep* steps = nullptr;
+  int nsteps = 0;
+  float c_pre = 0.f, noise_std = 0.f;
+};
+
+int get_program(const std::string& key, const SsmProgram& prog, std::shared_ptr<DeviceProgram>* out);
+int get_twiddle(long long n, float2** out);
+int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, const float* wave_scale,
+                uint64_t seed, uint64_t counter, cudaStream_t st);
+
+}  // namespace ldbp

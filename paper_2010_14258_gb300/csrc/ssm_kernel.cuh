@@ -1,0 +1,228 @@
+// Cluster-resident split-step Fourier kernel (plain SSM channel and full DBP).
+//
+// Every step of Eqs. (6)/(8) is  u <- sigma( iDFT( H . DFT(u) ) )  (with the
+// half-steps of the symmetric method merged across step boundaries, and the
+// ASE of an amplifier added in the spectral domain).  A waveform of
+// n = P * N2 samples lives in the shared memory of a thread-block cluster of
+// P blocks for ALL steps: HBM is touched once to load and once to store.
+//
+// Transform (Cooley-Tukey with n = P * N2, "four-step" split):
+//   block r holds the decimated sequence x_r[m2] = x[r + P m2];
+//   1. local N2-point Stockham FFT in shared memory (radix 16, conflict-free
+//      padded layout): Y_r[k2];
+//   2. each block takes a chunk of k2 and, for every r, reads Y_r[k2] from the
+//      peer's shared memory (DSMEM), multiplies by exp(-j 2 pi r k2 / n),
+//      runs the P-point DFT over r -> X[k2 + N2 k1], applies the step's
+//      spectral multiply (and noise), conjugates, runs the P-point DFT again,
+//      multiplies by the same twiddles and writes back to block r;
+//   3. local N2-point FFT of the conjugated data; conjugating its output gives
+//      the inverse transform, and the Kerr rotation is applied in registers
+//      before the result is stored.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "ssm.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ldbp {
+
+constexpr int kSsmE = 32;  // complex elements per thread
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Published definition (Salmon et al., SC'11): 10 rounds of
+// (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+// key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int rnd = 0; rnd < 10; ++rnd) {
+    if (rnd > 0) {
+      k.x += W0;
+      k.y += W1;
+    }
+    const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+    const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+// Complex normal with unit variance per component for ASE bin k (Box-Muller).
+__device__ __forceinline__ float2 ase_normal(uint32_t k, uint32_t b, uint32_t span, const SsmParams& p) {
+  const uint4 w = philox4x32_10(make_uint4(k >> 1, b, span, p.counter), make_uint2(p.seed_lo, p.seed_hi));
+  const uint32_t wa = (k & 1) ? w.z : w.x;
+  const uint32_t wb = (k & 1) ? w.w : w.y;
+  const float u1 = fmaf((float)wa, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float u2 = fmaf((float)wb, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+  const float rad = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(rad * c, rad * s);
+}
+
+// One radix-R Stockham pass of the local N2-point forward FFT (in place,
+// loads complete before stores).  Ns = product of the earlier radices.
+template <int LOGN2, int LOGNS, int LOGR, bool LAST_OF_INVERSE>
+__device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict__ tw, int P, float c) {
+  constexpr int N2 = 1 << LOGN2, R = 1 << LOGR, Ns = 1 << LOGNS, NT = N2 / kSsmE, NB = kSsmE / R;
+  constexpr int TSTRIDE = N2 / (Ns * R);  // twiddle exponent stride in W_N2 units
+  const int t = threadIdx.x;
+  float2 a[kSsmE];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = t + i * NT;
+#pragma unroll
+    for (int q = 0; q < R; ++q) a[i * R + q] = sbuf[spad(j + q * (N2 / R))];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = t + i * NT;
+    const int k = j & (Ns - 1);
+    if constexpr (Ns > 1) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) a[i * R + q] = cmul(a[i * R + q], __ldg(&tw[(q * k * TSTRIDE) * P]));
+    }
+    dft<R>(&a[i * R]);
+    if constexpr (LAST_OF_INVERSE) {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        float2 v = make_float2(a[i * R + q].x, -a[i * R + q].y);
+        if (c != 0.f) v = kerr_rotate_precise<true>(v, c);
+        a[i * R + q] = v;
+      }
+    }
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) sbuf[spad(base + q * Ns)] = a[i * R + q];
+  }
+  __syncthreads();
+}
+
+template <int LOGN2, int LOGNS, bool INVERSE>
+__device__ __forceinline__ void ssm_local_fft(float2* sbuf, const float2* tw, int P, float c) {
+  if constexpr (LOGNS < LOGN2) {
+    constexpr int LOGR = (LOGNS == 0 && (LOGN2 % 4) != 0) ? (LOGN2 % 4) : 4;
+    ssm_pass<LOGN2, LOGNS, LOGR, INVERSE && (LOGNS + LOGR == LOGN2)>(sbuf, tw, P, c);
+    ssm_local_fft<LOGN2, LOGNS + LOGR, INVERSE>(sbuf, tw, P, c);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl) {
+  if constexpr (P > 1) cl.sync();
+  else __syncthreads();
+}
+
+// Spectral step across the cluster (see file comment, step 2).
+template <int LOGN2, int P>
+__device__ __forceinline__ void ssm_middle(float2* sbuf, cg::cluster_group& cl, int r, int b, const SsmStep& st,
+                                           const SsmParams& p, bool first) {
+  constexpr int N2 = 1 << LOGN2, NT = N2 / kSsmE, C = N2 / P, NK = kSsmE / P;
+  const int t = threadIdx.x;
+  float2* rem[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) rem[q] = cl.map_shared_rank(sbuf, q);
+  const float2* __restrict__ H = p.tabs[st.tab];
+  const float2* __restrict__ HN = st.noise_tab >= 0 ? p.tabs[st.noise_tab] : nullptr;
+  const bool noise = st.noise_tab > -2;
+  const float flat = 1.0f / (float)p.n;
+  float sc = st.scale;
+  if (first && p.wave_scale) sc *= p.wave_scale[b];
+  float2 out[NK][P];
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int k2 = r * C + t + i * NT;
+    float2 a[P], w[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) a[q] = rem[q][spad(k2)];
+    w[0] = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int q = 1; q < P; ++q) {
+      w[q] = __ldg(&p.twiddle[q * k2]);
+      a[q] = cmul(a[q], w[q]);
+    }
+    dft<P>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+      const int k = k2 + N2 * k1;
+      const float2 h = __ldg(&H[k]);
+      float2 A = cmul(a[k1], make_float2(h.x * sc, h.y * sc));
+      if (noise) {
+        const float2 g = ase_normal((uint32_t)k, (uint32_t)b, (uint32_t)st.span, p);
+        const float2 hn = HN ? __ldg(&HN[k]) : make_float2(flat, 0.f);
+        A = cadd(A, cmul(hn, make_float2(g.x * p.noise_std, g.y * p.noise_std)));
+      }
+      a[k1] = make_float2(A.x, -A.y);
+    }
+    dft<P>(a);
+#pragma unroll
+    for (int q = 0; q < P; ++q) out[i][q] = cmul(a[q], w[q]);
+  }
+  cluster_barrier<P>(cl);  // every read of the peers' spectra has completed
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int k2 = r * C + t + i * NT;
+#pragma unroll
+    for (int q = 0; q < P; ++q) rem[q][spad(k2)] = out[i][q];
+  }
+  cluster_barrier<P>(cl);  // every write has landed before the local transforms
+}
+
+template <int LOGN2, int P>
+__global__ void __launch_bounds__((1 << LOGN2) / kSsmE, 1) ssm_kernel(const __grid_constant__ SsmParams p) {
+  constexpr int N2 = 1 << LOGN2, NT = N2 / kSsmE;
+  extern __shared__ __align__(16) float2 sbuf[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int r = (int)cl.block_rank();
+  const int b = blockIdx.x / P;
+  const int t = threadIdx.x;
+  const long long n = p.n;
+  const float2* __restrict__ xin = p.x + (long long)b * n;
+  for (int m2 = t; m2 < N2; m2 += NT) {
+    float2 v = xin[r + (long long)P * m2];
+    if (p.c_pre != 0.f) v = kerr_rotate_precise<true>(v, p.c_pre);
+    sbuf[spad(m2)] = v;
+  }
+  __syncthreads();
+  for (int s = 0; s < p.nsteps; ++s) {
+    const SsmStep st = p.steps[s];
+    ssm_local_fft<LOGN2, 0, false>(sbuf, p.twiddle, P, 0.f);
+    cluster_barrier<P>(cl);  // all spectra of the cluster are ready
+    ssm_middle<LOGN2, P>(sbuf, cl, r, b, st, p, s == 0);
+    ssm_local_fft<LOGN2, 0, true>(sbuf, p.twiddle, P, st.c);
+  }
+  float2* __restrict__ yout = p.y + (long long)b * n;
+  for (int m2 = t; m2 < N2; m2 += NT) yout[r + (long long)P * m2] = sbuf[spad(m2)];
+}
+
+template <int LOGN2, int P>
+cudaError_t launch_one(const SsmParams& p, cudaStream_t st) {
+  constexpr int N2 = 1 << LOGN2, NT = N2 / kSsmE;
+  const size_t smem = sizeof(float2) * (size_t)(N2 + N2 / 16);
+  auto kern = ssm_kernel<LOGN2, P>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (P > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(p.batch * P));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = P;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, p);
+}
+
+}  // namespace ldbp

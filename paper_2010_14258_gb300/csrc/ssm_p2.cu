@@ -1,0 +1,9 @@
+// Instances of the split-step kernel with cluster size 2.
+#include "ssm_kernel.cuh"
+
+namespace ldbp {
+template cudaError_t launch_one<11, 2>(const SsmParams& p, cudaStream_t st);
+template cudaError_t launch_one<12, 2>(const SsmParams& p, cudaStream_t st);
+template cudaError_t launch_one<13, 2>(const SsmParams& p, cudaStream_t st);
+template cudaError_t launch_one<14, 2>(const SsmParams& p, cudaStream_t st);
+}  // namespace ldbp

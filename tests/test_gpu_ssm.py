@@ -1,0 +1,131 @@
+"""Parity of the cluster-resident split-step kernel (channel and DBP) with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import nlse, txrx
+from tests.util import c64, gpu_lib, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _sig(B, n, seed, pw, sps=2):
+    s = synth.qam16_symbols(B, n // sps, seed)
+    return c64(txrx.tx(s, sps, 0.1, pw))
+
+
+def _channel(x, fiber, link, fs):
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    y = api.ssm_forward(fiber, link, fs, to_dev(x))
+    torch.cuda.synchronize()
+    return to_np(y)
+
+
+def _dbp(x, fiber, link, fs, N, sym):
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    y = api.dbp_apply(fiber, link, fs, to_dev(x), steps_per_span=N, symmetric=sym)
+    torch.cuda.synchronize()
+    return to_np(y)
+
+
+# (n, B) pairs select every cluster size 1, 2, 4, 8, 16 (see ssm_choose_cluster)
+SHAPES = [(512, 3), (1024, 2), (4096, 1), (16384, 1), (65536, 2), (131072, 1), (32768, 64)]
+
+
+@pytest.mark.parametrize("n,B", SHAPES)
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_channel_parity_shapes(n, B, symmetric):
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(2, 80.0, 3, symmetric, False)
+    Bt = min(B, 4)
+    x = _sig(B, n, n + B, 2e-3)
+    y = _channel(x, fib, link, fs)
+    ref = nlse.channel(x[:Bt], fib, link, fs)
+    assert rel_l2(y[:Bt], ref) <= 1e-5 * (2 * 3 + 1)
+
+
+def test_single_step_error():
+    fs = 20e9
+    fib = synth.Fiber()
+    x = _sig(2, 8192, 1, 5e-3)
+    link = synth.Link(1, 0.5, 1, True, False)
+    y = _channel(x, fib, link, fs)
+    ref = nlse.channel(x, fib, link, fs)
+    assert rel_l2(y, ref) <= 1e-5
+
+
+def test_channel_with_ase_matches_philox_oracle():
+    fs = 20e9
+    fib = synth.Fiber()
+    for sym in (True, False):
+        link = synth.Link(3, 80.0, 4, sym, True, 5.0, 1.946e14, seed=0x1234567890ABCDEF, counter=17)
+        x = _sig(3, 4096, 7, 1e-3)
+        y = _channel(x, fib, link, fs)
+        ref = nlse.channel(x, fib, link, fs)
+        assert rel_l2(y, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("symmetric,N", [(True, 1), (False, 1), (True, 3), (False, 2)])
+def test_dbp_parity(symmetric, N):
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(4, 80.0, 5, True, False)
+    x = _sig(2, 16384, 3, 2e-3)
+    y = nlse.channel(x, fib, link, fs)
+    yc = c64(y)
+    out = _dbp(yc, fib, link, fs, N, symmetric)
+    ref = nlse.dbp(yc, fib, link, fs, steps_per_span=N, symmetric=symmetric)
+    assert rel_l2(out, ref) <= 1e-5 * (4 * N + 1)
+
+
+def test_dbp_inverts_channel_on_same_grid():
+    fs = 20e9
+    fib = synth.Fiber()
+    for sym in (True, False):
+        link = synth.Link(3, 80.0, 6, sym, False)
+        x = _sig(2, 8192, 5, 4e-3)
+        y = _channel(x, fib, link, fs)
+        xr = _dbp(c64(y), fib, link, fs, 6, sym)
+        assert rel_l2(xr, x) <= 1e-4
+
+
+@pytest.mark.slow
+def test_plain_ssm_16k_500_steps_then_dbp():
+    # 8192 16-QAM symbols at 10 GBd, 2 sps; 10 x 80 km, 50 symmetric steps/span, 2 dBm; 1-StPS DBP
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(10, 80.0, 50, True, False)
+    s = synth.qam16_symbols(1, 8192, 1)
+    pw = 10 ** (2.0 / 10) * 1e-3
+    x = c64(txrx.tx(s, 2, 0.1, pw))
+    y = _channel(x, fib, link, fs)
+    ref = nlse.channel(x, fib, link, fs)
+    assert rel_l2(y, ref) <= 1e-4
+    z = _dbp(c64(y), fib, link, fs, 1, True)
+    zr = nlse.dbp(c64(y), fib, link, fs, steps_per_span=1, symmetric=True)
+    assert rel_l2(z, zr) <= 1e-4
+    snr_gpu = txrx.evaluate(z, s, 2, 0.1, pw)["snr_db"]
+    snr_ref = txrx.evaluate(zr, s, 2, 0.1, pw)["snr_db"]
+    assert abs(snr_gpu - snr_ref) <= 0.01
+
+
+def test_full_size_dbp_sampled():
+    # 256 x 65536, 25 x 80 km, 1 StPS asymmetric DBP: sampled waveforms vs the oracle
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(25, 80.0, 1, False, False)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    x = torch.randn(256, 65536, generator=g, device="cuda", dtype=torch.complex64) * (1e-3 ** 0.5)
+    y = api.dbp_apply(fib, link, fs, x, steps_per_span=1, symmetric=False)
+    torch.cuda.synchronize()
+    for b in (0, 131, 255):
+        ref = nlse.dbp(to_np(x[b]), fib, link, fs, steps_per_span=1, symmetric=False)
+        assert rel_l2(to_np(y[b]), ref) <= 1e-4
