@@ -133,7 +133,7 @@ typedef struct {
  *  fs_hz         sampling rate of the waveform.
  *  x             device complex64 [batch][n] launch waveform in sqrt(W).
  *  y             device complex64 [batch][n]; may equal x (in place).
- *  n             power of two, 512 <= n <= 262144.
+ *  n             power of two, 512 <= n <= 131072.
  * One kernel launch runs all steps; each waveform stays in the shared memory
  * of a thread-block cluster.  The first call for a given (device, fiber,
  * link, fs, n) computes the FP64 spectral tables and uploads them into
@@ -159,6 +159,56 @@ int ssm_forward(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, co
  */
 int dbp_apply(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, int32_t steps_per_span,
               int32_t symmetric, const void* x, void* y, int64_t n, int32_t batch, void* stream);
+
+/*
+ * ssm_cufft -- the same split-step programs as ssm_forward (dbp_steps_per_span
+ * == 0) or dbp_apply (dbp_steps_per_span >= 1, dbp_symmetric) executed with
+ * the cuFFT library: per step a batched C2C FFT, a spectral-multiply kernel,
+ * an inverse FFT and a Kerr kernel.  Provided only as the library-FFT
+ * comparison for the fused kernel; results agree with ssm_forward/dbp_apply
+ * to FP32 rounding.  cuFFT allocates its own work area on the first call for
+ * a given (n, batch).  Arguments and errors as ssm_forward.
+ */
+int ssm_cufft(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, int32_t dbp_steps_per_span,
+              int32_t dbp_symmetric, const void* x, void* y, int64_t n, int32_t batch, void* stream);
+
+/*
+ * ldbp_tx -- transmit waveform of Eq. (11), sampled at sps samples/symbol.
+ *
+ * x_b = sqrt(P_b sps) * iDFT( H_rrc . DFT(upsample(s_b)) ), with
+ * H_rrc(f) = sqrt(sps RC(f / R_s)) the root-raised-cosine response of the
+ * given roll-off (RC the raised-cosine spectrum) on the fftfreq grid; the
+ * symbol sequence is periodic, so the waveform is circular.  For unit-energy
+ * symbols the mean power is P_b.
+ *  symbols  device complex64 [batch][nsym]
+ *  power_w  device float [batch], launch power per waveform in W
+ *  x        device complex64 [batch][nsym * sps] (output)
+ * nsym * sps must be a power of two in [512, 131072]; 0 < rolloff <= 1.
+ * Errors: LDBP_EINVAL, LDBP_ECUDA.
+ */
+int ldbp_tx(const void* symbols, const float* power_w, int32_t sps, double rolloff, void* x, int64_t nsym,
+            int32_t batch, void* stream);
+
+/*
+ * ldbp_rx -- receiver chain of Eq. (12), loss and its gradient (Sec. IV-B).
+ *
+ * s_tilde_b = (M y_b) / sqrt(P_b sps): matched RRC filter (the ldbp_tx
+ * response) and every sps-th sample from offset 0; phi_b = arg(s_b^H s_tilde_b)
+ * (genie-aided phase correction); mse_b = ||s_tilde_b e^{-j phi_b} - s_b||^2 / nsym.
+ * If grad != NULL it receives g = d l / d y with l = grad_scale / 2 * sum_b
+ * ||s_hat_b - s_b||^2 (phi held constant, the matched filter being real and
+ * even); grad_scale = 2 / (nsym * batch) gives the batch-mean MSE.
+ *  y          device complex64 [batch][n], n = nsym * sps
+ *  symbols    device complex64 [batch][nsym]
+ *  power_w    device float [batch]
+ *  stats      device double [batch][2] (output): mse_b and the mean |s_b|^2
+ *  phi        device float [batch] (output)
+ *  grad       device complex64 [batch][n] or NULL (output; may not alias y)
+ *  workspace  device complex64 [batch][n] scratch owned by the caller
+ * Errors: LDBP_EINVAL, LDBP_ECUDA.
+ */
+int ldbp_rx(const void* y, const void* symbols, const float* power_w, int32_t sps, double rolloff, int64_t nsym,
+            int32_t batch, double* stats, float* phi, void* grad, float grad_scale, void* workspace, void* stream);
 
 /*
  * ldbp_ubench -- arithmetic ceilings of the current device (synchronous).

@@ -40,6 +40,11 @@ _SIGNATURES = {
                             c_int64, c_int32, c_void_p]),
     "dbp_apply": (c_int, [ctypes.POINTER(LdbpFiber), ctypes.POINTER(LdbpLink), c_double, c_int32, c_int32,
                           c_void_p, c_void_p, c_int64, c_int32, c_void_p]),
+    "ssm_cufft": (c_int, [ctypes.POINTER(LdbpFiber), ctypes.POINTER(LdbpLink), c_double, c_int32, c_int32,
+                          c_void_p, c_void_p, c_int64, c_int32, c_void_p]),
+    "ldbp_tx": (c_int, [c_void_p, c_void_p, c_int32, c_double, c_void_p, c_int64, c_int32, c_void_p]),
+    "ldbp_rx": (c_int, [c_void_p, c_void_p, c_void_p, c_int32, c_double, c_int64, c_int32, c_void_p, c_void_p,
+                        c_void_p, c_float, c_void_p, c_void_p]),
     "ldbp_ubench": (c_int, [c_int32, ctypes.POINTER(c_double)]),
     "ldbp_apply": (c_int, [c_void_p, c_int32, P_int32, P_float, c_int32, c_void_p, c_void_p, c_int64, c_int32,
                            c_void_p, c_void_p]),

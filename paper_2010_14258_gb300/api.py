@@ -99,3 +99,59 @@ def dbp_apply(fiber, link, fs, x, steps_per_span=1, symmetric=False, out=None):
     _lib.check(_lib.lib().dbp_apply(ctypes.byref(f), ctypes.byref(l), float(fs), int(steps_per_span),
                                     int(bool(symmetric)), _ptr(x2), _ptr(y), x2.shape[1], x2.shape[0], _stream()))
     return y[0] if squeeze else y
+
+
+def ssm_cufft(fiber, link, fs, x, dbp_steps_per_span=0, dbp_symmetric=False, out=None):
+    """The same split-step program run with cuFFT (comparison path only)."""
+    import ctypes
+    x2, squeeze = _batched(x)
+    y = torch.empty_like(x2) if out is None else out
+    f, l = fiber_struct(fiber), link_struct(link)
+    _lib.check(_lib.lib().ssm_cufft(ctypes.byref(f), ctypes.byref(l), float(fs), int(dbp_steps_per_span),
+                                    int(bool(dbp_symmetric)), _ptr(x2), _ptr(y), x2.shape[1], x2.shape[0], _stream()))
+    return y[0] if squeeze else y
+
+
+def _power_tensor(power_w, B):
+    if isinstance(power_w, torch.Tensor):
+        p = power_w.to(device="cuda", dtype=torch.float32).reshape(-1)
+    else:
+        p = torch.as_tensor(power_w, dtype=torch.float32).reshape(-1).cuda()
+    if p.numel() == 1 and B > 1:
+        p = p.expand(B).contiguous()
+    if p.numel() != B:
+        raise ValueError("power_w must be a scalar or have one entry per waveform")
+    return p.contiguous()
+
+
+def tx(symbols, power_w, sps=2, rolloff=0.1, out=None):
+    """Eq. (11): RRC-shaped waveform of 16-QAM (or any) symbols at power P (W)."""
+    _check_c64("symbols", symbols)
+    B, nsym = symbols.shape
+    p = _power_tensor(power_w, B)
+    x = torch.empty((B, nsym * sps), dtype=torch.complex64, device=symbols.device) if out is None else out
+    _lib.check(_lib.lib().ldbp_tx(_ptr(symbols), _ptr(p), int(sps), float(rolloff), _ptr(x), nsym, B, _stream()))
+    return x
+
+
+def rx(y, symbols, power_w, sps=2, rolloff=0.1, grad=False, grad_scale=None, workspace=None):
+    """Eq. (12) receiver: returns (stats[B, 2] float64 = (mse_b, mean |s_b|^2), phi[B] float32, grad or None)."""
+    _check_c64("y", y)
+    _check_c64("symbols", symbols)
+    B, n = y.shape
+    nsym = symbols.shape[1]
+    p = _power_tensor(power_w, B)
+    mse = torch.empty((B, 2), dtype=torch.float64, device=y.device)
+    phi = torch.empty(B, dtype=torch.float32, device=y.device)
+    ws = torch.empty_like(y) if workspace is None else workspace
+    g = torch.empty_like(y) if grad else None
+    gs = 2.0 / (nsym * B) if grad_scale is None else grad_scale
+    _lib.check(_lib.lib().ldbp_rx(_ptr(y), _ptr(symbols), _ptr(p), int(sps), float(rolloff), nsym, B, _ptr(mse),
+                                  _ptr(phi), _ptr(g), float(gs), _ptr(ws), _stream()))
+    return mse, phi, g
+
+
+def snr_db(stats):
+    """Effective SNR (Eq. (14), read as sum_b ||s_b||^2 / sum_b ||s_hat_b - s_b||^2) in dB."""
+    st = stats.double().cpu()
+    return float(10.0 * torch.log10(st[:, 1].sum() / st[:, 0].sum()).item())

@@ -29,17 +29,21 @@ struct SsmParams {
   int nsteps;
   const SsmStep* steps;                 // device [nsteps]
   const float2* tabs[kSsmMaxTabs];      // device [n] each, DFT order
-  const float2* twiddle;                // device [n]: exp(-j 2 pi t / n)
-  const float* wave_scale;              // device [batch] multiplier of step 0, or nullptr
+  const float2* twiddle;                // device twiddle buffer (layout in ssm_kernel.cuh)
+  const float* wave_scale;              // device [batch] per-waveform factor of step 0, or nullptr
+  int wave_mode;                        // factor = w, sqrt(w) or 1/sqrt(w) for mode 0, 1, 2
   float c_pre;                          // Kerr applied to the input before step 0 (0: none)
   float noise_std;                      // sqrt(n sigma^2 / 2)
   uint32_t seed_lo, seed_hi, counter;
 };
 
+// Number of twiddle entries for (P, N2).
+long long ssm_twiddle_count(int P, int log_n2);
 // Launches the kernel for waveform length n = P * N2 (both powers of two).
 cudaError_t launch_ssm(const SsmParams& p, int P, int log_n2, cudaStream_t st);
-// Largest supported per-block length.
-constexpr int kSsmMaxLogN2 = 14;
+// Largest supported per-block length and cluster size.
+constexpr int kSsmMaxLogN2 = 13;
+constexpr int kSsmMaxCluster = 16;
 constexpr int kSsmMinLogN2 = 9;
 // Chooses the cluster size for a batch of waveforms of length n (power of two).
 int ssm_choose_cluster(long long n, int batch, int sm_count, int* P, int* log_n2);

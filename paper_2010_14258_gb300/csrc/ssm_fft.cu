@@ -3,6 +3,7 @@
 // they compile in parallel.
 #include "common.cuh"
 #include "ssm.cuh"
+#include "ssm_kernel.cuh"
 
 namespace ldbp {
 
@@ -24,9 +25,12 @@ cudaError_t launch_ssm(const SsmParams& p, int P, int log_n2, cudaStream_t st) {
     case 11: switch (P) { LDBP_SSM_CASES(11) }
     case 12: switch (P) { LDBP_SSM_CASES(12) }
     case 13: switch (P) { LDBP_SSM_CASES(13) }
-    case 14: switch (P) { LDBP_SSM_CASES(14) }
     default: return cudaErrorInvalidValue;
   }
+}
+
+long long ssm_twiddle_count(int P, int log_n2) {
+  return (long long)(P - 1) * (1LL << log_n2) + ssm_stage_offset(log_n2, log_n2);
 }
 
 int ssm_choose_cluster(long long n, int batch, int sm_count, int* P, int* log_n2) {
@@ -35,6 +39,7 @@ int ssm_choose_cluster(long long n, int batch, int sm_count, int* P, int* log_n2
   if ((1LL << logn) != n || logn < kSsmMinLogN2 || logn > kSsmMaxLogN2 + 4) return -1;
   int p = 1;
   while (logn - __builtin_ctz(p) > kSsmMaxLogN2) p *= 2;
+  if (p > kSsmMaxCluster) return -1;
   // more blocks per waveform while the batch alone does not fill the GPU
   while (p < 16 && logn - __builtin_ctz(p) - 1 >= 11 && (long long)batch * p < sm_count) p *= 2;
   *P = p;

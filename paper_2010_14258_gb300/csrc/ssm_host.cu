@@ -127,18 +127,33 @@ static cudaError_t upload_c64(const std::vector<std::complex<double>>& v, float2
   return cudaMemcpy(*out, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
 }
 
-int get_twiddle(long long n, float2** out) {
+int get_twiddle(long long n, int P, int log_n2, float2** out) {
   int dev = 0;
   LDBP_CUDA_TRY(cudaGetDevice(&dev));
-  const std::string key = std::to_string(dev) + ":" + std::to_string(n);
+  const std::string key = std::to_string(dev) + ":" + std::to_string(n) + ":" + std::to_string(P);
   std::lock_guard<std::mutex> lk(g_cache_mu);
   auto it = g_twiddles.find(key);
   if (it != g_twiddles.end()) {
     *out = it->second;
     return 0;
   }
-  std::vector<std::complex<double>> w((size_t)n);
-  for (long long t = 0; t < n; ++t) w[(size_t)t] = std::polar(1.0, -2.0 * kPi * (double)t / (double)n);
+  const long long N2 = 1LL << log_n2;
+  std::vector<std::complex<double>> w((size_t)ssm_twiddle_count(P, log_n2));
+  for (int q = 1; q < P; ++q)
+    for (long long k2 = 0; k2 < N2; ++k2)
+      w[(size_t)((q - 1) * N2 + k2)] = std::polar(1.0, -2.0 * kPi * (double)(q * k2) / (double)n);
+  size_t off = (size_t)(P - 1) * (size_t)N2;
+  for (int logns = 0; logns < log_n2;) {
+    const int logr = (logns == 0 && (log_n2 % 4) != 0) ? (log_n2 % 4) : 4;
+    const long long Ns = 1LL << logns, R = 1LL << logr;
+    if (logns > 0) {
+      for (long long q = 1; q < R; ++q)
+        for (long long k = 0; k < Ns; ++k)
+          w[off + (size_t)((q - 1) * Ns + k)] = std::polar(1.0, -2.0 * kPi * (double)(q * k) / (double)(Ns * R));
+      off += (size_t)((R - 1) * Ns);
+    }
+    logns += logr;
+  }
   float2* d = nullptr;
   cudaError_t e = upload_c64(w, &d);
   if (e != cudaSuccess) return cuda_fail(e, "twiddle table");
@@ -169,6 +184,7 @@ int get_program(const std::string& key_in, const SsmProgram& prog, std::shared_p
   e = cudaMemcpy(dp->steps, prog.steps.data(), prog.steps.size() * sizeof(SsmStep), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "ssm steps copy");
   dp->nsteps = (int)prog.steps.size();
+  dp->host_steps = prog.steps;
   dp->c_pre = (float)prog.c_pre;
   dp->noise_std = (float)prog.noise_std;
   g_programs[key] = dp;
@@ -183,7 +199,7 @@ static std::string fkey(const ldbp_fiber& f, double fs, long long n) {
   return buf;
 }
 
-static int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x, const void* y, long long n,
+int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x, const void* y, long long n,
                       int batch) {
   if (!f || !l || !x || !y) return fail(LDBP_EINVAL, "fiber, link, x and y must be non-NULL");
   if (!(fs > 0.0) || !std::isfinite(fs)) return fail(LDBP_EINVAL, "fs_hz must be positive");
@@ -201,14 +217,14 @@ static int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const 
 }
 
 int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, const float* wave_scale,
-                uint64_t seed, uint64_t counter, cudaStream_t st) {
+                int wave_mode, uint64_t seed, uint64_t counter, cudaStream_t st) {
   int sms = 0, dev = 0;
   LDBP_CUDA_TRY(cudaGetDevice(&dev));
   LDBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   int P = 1, log_n2 = 0;
   if (ssm_choose_cluster(n, batch, sms, &P, &log_n2)) return fail(LDBP_EINVAL, "unsupported n=%lld", n);
   float2* tw = nullptr;
-  if (int rc = get_twiddle(n, &tw)) return rc;
+  if (int rc = get_twiddle(n, P, log_n2, &tw)) return rc;
   SsmParams p;
   memset(&p, 0, sizeof(p));
   p.x = static_cast<const float2*>(x);
@@ -220,6 +236,7 @@ int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, in
   for (size_t i = 0; i < dp.tabs.size() && i < (size_t)kSsmMaxTabs; ++i) p.tabs[i] = dp.tabs[i];
   p.twiddle = tw;
   p.wave_scale = wave_scale;
+  p.wave_mode = wave_mode;
   p.c_pre = dp.c_pre;
   p.noise_std = dp.noise_std;
   p.seed_lo = (uint32_t)(seed & 0xffffffffu);
@@ -228,6 +245,27 @@ int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, in
   cudaError_t e = launch_ssm(p, P, log_n2, st);
   if (e != cudaSuccess) return cuda_fail(e, "ssm launch");
   return 0;
+}
+
+int link_program(const ldbp_fiber& f, const ldbp_link& l, double fs, long long n, int dbp_steps, bool dbp_symmetric,
+                 std::shared_ptr<DeviceProgram>* out) {
+  char buf[256];
+  if (dbp_steps == 0)
+    snprintf(buf, sizeof(buf), "ch|%d,%.17g,%d,%d,%d,%.17g,%.17g", l.n_spans, l.span_km, l.steps_per_span,
+             l.symmetric ? 1 : 0, l.ase ? 1 : 0, l.nf_db, l.carrier_hz);
+  else
+    snprintf(buf, sizeof(buf), "dbp|%d,%.17g,%d,%d", l.n_spans, l.span_km, dbp_steps, dbp_symmetric ? 1 : 0);
+  const std::string key = fkey(f, fs, n) + buf;
+  int dev = 0;
+  LDBP_CUDA_TRY(cudaGetDevice(&dev));
+  bool need = true;
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    need = g_programs.find(std::to_string(dev) + "|" + key) == g_programs.end();
+  }
+  SsmProgram prog;
+  if (need) prog = dbp_steps == 0 ? build_channel(f, l, fs, n) : build_dbp(f, l, fs, n, dbp_steps, dbp_symmetric);
+  return get_program(key, prog, out);
 }
 
 }  // namespace ldbp
@@ -239,46 +277,18 @@ extern "C" {
 int ssm_forward(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, const void* x, void* y, int64_t n,
                 int32_t batch, void* stream) {
   if (int rc = check_link(fiber, link, fs_hz, x, y, n, batch)) return rc;
-  char buf[256];
-  snprintf(buf, sizeof(buf), "ch|%d,%.17g,%d,%d,%d,%.17g,%.17g", link->n_spans, link->span_km,
-           link->steps_per_span, link->symmetric, link->ase, link->nf_db, link->carrier_hz);
-  const std::string key = fkey(*fiber, fs_hz, n) + buf;
   std::shared_ptr<DeviceProgram> dp;
-  {
-    // building the FP64 tables only on a cache miss
-    int dev = 0;
-    LDBP_CUDA_TRY(cudaGetDevice(&dev));
-    SsmProgram prog;
-    bool need = true;
-    {
-      std::lock_guard<std::mutex> lk(g_cache_mu);
-      need = g_programs.find(std::to_string(dev) + "|" + key) == g_programs.end();
-    }
-    if (need) prog = build_channel(*fiber, *link, fs_hz, n);
-    if (int rc = get_program(key, prog, &dp)) return rc;
-  }
-  return run_program(*dp, x, y, n, batch, nullptr, link->seed, link->counter, static_cast<cudaStream_t>(stream));
+  if (int rc = link_program(*fiber, *link, fs_hz, n, 0, false, &dp)) return rc;
+  return run_program(*dp, x, y, n, batch, nullptr, 0, link->seed, link->counter, static_cast<cudaStream_t>(stream));
 }
 
 int dbp_apply(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, int32_t steps_per_span,
               int32_t symmetric, const void* x, void* y, int64_t n, int32_t batch, void* stream) {
   if (int rc = check_link(fiber, link, fs_hz, x, y, n, batch)) return rc;
   if (steps_per_span < 1) return fail(LDBP_EINVAL, "steps_per_span=%d must be >= 1", steps_per_span);
-  char buf[256];
-  snprintf(buf, sizeof(buf), "dbp|%d,%.17g,%d,%d", link->n_spans, link->span_km, steps_per_span, symmetric ? 1 : 0);
-  const std::string key = fkey(*fiber, fs_hz, n) + buf;
   std::shared_ptr<DeviceProgram> dp;
-  int dev = 0;
-  LDBP_CUDA_TRY(cudaGetDevice(&dev));
-  SsmProgram prog;
-  bool need = true;
-  {
-    std::lock_guard<std::mutex> lk(g_cache_mu);
-    need = g_programs.find(std::to_string(dev) + "|" + key) == g_programs.end();
-  }
-  if (need) prog = build_dbp(*fiber, *link, fs_hz, n, steps_per_span, symmetric != 0);
-  if (int rc = get_program(key, prog, &dp)) return rc;
-  return run_program(*dp, x, y, n, batch, nullptr, 0, 0, static_cast<cudaStream_t>(stream));
+  if (int rc = link_program(*fiber, *link, fs_hz, n, steps_per_span, symmetric != 0, &dp)) return rc;
+  return run_program(*dp, x, y, n, batch, nullptr, 0, 0, 0, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -32,14 +32,20 @@ SsmProgram build_dbp(const ldbp_fiber& f, const ldbp_link& l, double fs, long lo
 
 struct DeviceProgram {
   std::vector<float2*> tabs;
+  std::vector<SsmStep> host_steps;
   SsmStep* steps = nullptr;
   int nsteps = 0;
   float c_pre = 0.f, noise_std = 0.f;
 };
 
 int get_program(const std::string& key, const SsmProgram& prog, std::shared_ptr<DeviceProgram>* out);
-int get_twiddle(long long n, float2** out);
+// Cached program of the channel (dbp_steps == 0) or of DBP; tables built on a miss.
+int link_program(const ldbp_fiber& f, const ldbp_link& l, double fs, long long n, int dbp_steps, bool dbp_symmetric,
+                 std::shared_ptr<DeviceProgram>* out);
+int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x, const void* y, long long n,
+               int batch);
+int get_twiddle(long long n, int P, int log_n2, float2** out);
 int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, const float* wave_scale,
-                uint64_t seed, uint64_t counter, cudaStream_t st);
+                int wave_mode, uint64_t seed, uint64_t counter, cudaStream_t st);
 
 }  // namespace ldbp

@@ -24,51 +24,34 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "ssm.cuh"
+#include "philox.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace ldbp {
 
-constexpr int kSsmE = 32;  // complex elements per thread
+constexpr int kSsmE = 16;  // complex elements per thread
 
-// ---------------------------------------------------------------- Philox4x32-10
-// Published definition (Salmon et al., SC'11): 10 rounds of
-// (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
-// key bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-  for (int rnd = 0; rnd < 10; ++rnd) {
-    if (rnd > 0) {
-      k.x += W0;
-      k.y += W1;
-    }
-    const uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
-    const uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+// Twiddle layout (one device buffer per (n, P, N2)):
+//   [(q-1) N2 + k2]           = exp(-j 2 pi q k2 / n),     q = 1..P-1 (cluster step)
+//   stage(Ns) + [(q-1) Ns + k] = exp(-j 2 pi q k / (Ns R)), q = 1..R-1 (local pass with Ns > 1)
+// so that consecutive threads read consecutive entries.
+__host__ __device__ constexpr int ssm_stage_offset(int logn2, int logns_target) {
+  int off = 0, logns = 0;
+  while (logns < logns_target) {
+    const int logr = (logns == 0 && (logn2 % 4) != 0) ? (logn2 % 4) : 4;
+    if (logns > 0) off += ((1 << logr) - 1) << logns;
+    logns += logr;
   }
-  return c;
-}
-
-// Complex normal with unit variance per component for ASE bin k (Box-Muller).
-__device__ __forceinline__ float2 ase_normal(uint32_t k, uint32_t b, uint32_t span, const SsmParams& p) {
-  const uint4 w = philox4x32_10(make_uint4(k >> 1, b, span, p.counter), make_uint2(p.seed_lo, p.seed_hi));
-  const uint32_t wa = (k & 1) ? w.z : w.x;
-  const uint32_t wb = (k & 1) ? w.w : w.y;
-  const float u1 = fmaf((float)wa, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-  const float u2 = fmaf((float)wb, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-  const float rad = sqrtf(-2.0f * logf(u1));
-  float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  return make_float2(rad * c, rad * s);
+  return off;
 }
 
 // One radix-R Stockham pass of the local N2-point forward FFT (in place,
 // loads complete before stores).  Ns = product of the earlier radices.
 template <int LOGN2, int LOGNS, int LOGR, bool LAST_OF_INVERSE>
-__device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict__ tw, int P, float c) {
+__device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict__ stw, float c) {
   constexpr int N2 = 1 << LOGN2, R = 1 << LOGR, Ns = 1 << LOGNS, NT = N2 / kSsmE, NB = kSsmE / R;
-  constexpr int TSTRIDE = N2 / (Ns * R);  // twiddle exponent stride in W_N2 units
+  const float2* __restrict__ tw = stw + ssm_stage_offset(LOGN2, LOGNS);
   const int t = threadIdx.x;
   float2 a[kSsmE];
 #pragma unroll
@@ -84,7 +67,7 @@ __device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict_
     const int k = j & (Ns - 1);
     if constexpr (Ns > 1) {
 #pragma unroll
-      for (int q = 1; q < R; ++q) a[i * R + q] = cmul(a[i * R + q], __ldg(&tw[(q * k * TSTRIDE) * P]));
+      for (int q = 1; q < R; ++q) a[i * R + q] = cmul(a[i * R + q], __ldg(&tw[(q - 1) * Ns + k]));
     }
     dft<R>(&a[i * R]);
     if constexpr (LAST_OF_INVERSE) {
@@ -103,11 +86,11 @@ __device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict_
 }
 
 template <int LOGN2, int LOGNS, bool INVERSE>
-__device__ __forceinline__ void ssm_local_fft(float2* sbuf, const float2* tw, int P, float c) {
+__device__ __forceinline__ void ssm_local_fft(float2* sbuf, const float2* stw, float c) {
   if constexpr (LOGNS < LOGN2) {
     constexpr int LOGR = (LOGNS == 0 && (LOGN2 % 4) != 0) ? (LOGN2 % 4) : 4;
-    ssm_pass<LOGN2, LOGNS, LOGR, INVERSE && (LOGNS + LOGR == LOGN2)>(sbuf, tw, P, c);
-    ssm_local_fft<LOGN2, LOGNS + LOGR, INVERSE>(sbuf, tw, P, c);
+    ssm_pass<LOGN2, LOGNS, LOGR, INVERSE && (LOGNS + LOGR == LOGN2)>(sbuf, stw, c);
+    ssm_local_fft<LOGN2, LOGNS + LOGR, INVERSE>(sbuf, stw, c);
   }
 }
 
@@ -131,7 +114,10 @@ __device__ __forceinline__ void ssm_middle(float2* sbuf, cg::cluster_group& cl, 
   const bool noise = st.noise_tab > -2;
   const float flat = 1.0f / (float)p.n;
   float sc = st.scale;
-  if (first && p.wave_scale) sc *= p.wave_scale[b];
+  if (first && p.wave_scale) {
+    const float w = p.wave_scale[b];
+    sc *= p.wave_mode == 1 ? sqrtf(w) : p.wave_mode == 2 ? rsqrtf(w) : w;
+  }
   float2 out[NK][P];
 #pragma unroll
   for (int i = 0; i < NK; ++i) {
@@ -142,7 +128,7 @@ __device__ __forceinline__ void ssm_middle(float2* sbuf, cg::cluster_group& cl, 
     w[0] = make_float2(1.f, 0.f);
 #pragma unroll
     for (int q = 1; q < P; ++q) {
-      w[q] = __ldg(&p.twiddle[q * k2]);
+      w[q] = __ldg(&p.twiddle[(q - 1) * N2 + k2]);
       a[q] = cmul(a[q], w[q]);
     }
     dft<P>(a);
@@ -152,7 +138,7 @@ __device__ __forceinline__ void ssm_middle(float2* sbuf, cg::cluster_group& cl, 
       const float2 h = __ldg(&H[k]);
       float2 A = cmul(a[k1], make_float2(h.x * sc, h.y * sc));
       if (noise) {
-        const float2 g = ase_normal((uint32_t)k, (uint32_t)b, (uint32_t)st.span, p);
+        const float2 g = ase_normal((uint32_t)k, (uint32_t)b, (uint32_t)st.span, p.counter, p.seed_lo, p.seed_hi);
         const float2 hn = HN ? __ldg(&HN[k]) : make_float2(flat, 0.f);
         A = cadd(A, cmul(hn, make_float2(g.x * p.noise_std, g.y * p.noise_std)));
       }
@@ -173,7 +159,7 @@ __device__ __forceinline__ void ssm_middle(float2* sbuf, cg::cluster_group& cl, 
 }
 
 template <int LOGN2, int P>
-__global__ void __launch_bounds__((1 << LOGN2) / kSsmE, 1) ssm_kernel(const __grid_constant__ SsmParams p) {
+__global__ void __launch_bounds__((1 << LOGN2) / kSsmE, (512 / ((1 << LOGN2) / kSsmE)) > 1 ? (512 / ((1 << LOGN2) / kSsmE)) : 1) ssm_kernel(const __grid_constant__ SsmParams p) {
   constexpr int N2 = 1 << LOGN2, NT = N2 / kSsmE;
   extern __shared__ __align__(16) float2 sbuf[];
   cg::cluster_group cl = cg::this_cluster();
@@ -188,12 +174,13 @@ __global__ void __launch_bounds__((1 << LOGN2) / kSsmE, 1) ssm_kernel(const __gr
     sbuf[spad(m2)] = v;
   }
   __syncthreads();
+  const float2* stw = p.twiddle + (P - 1) * N2;
   for (int s = 0; s < p.nsteps; ++s) {
     const SsmStep st = p.steps[s];
-    ssm_local_fft<LOGN2, 0, false>(sbuf, p.twiddle, P, 0.f);
+    ssm_local_fft<LOGN2, 0, false>(sbuf, stw, 0.f);
     cluster_barrier<P>(cl);  // all spectra of the cluster are ready
     ssm_middle<LOGN2, P>(sbuf, cl, r, b, st, p, s == 0);
-    ssm_local_fft<LOGN2, 0, true>(sbuf, p.twiddle, P, st.c);
+    ssm_local_fft<LOGN2, 0, true>(sbuf, stw, st.c);
   }
   float2* __restrict__ yout = p.y + (long long)b * n;
   for (int m2 = t; m2 < N2; m2 += NT) yout[r + (long long)P * m2] = sbuf[spad(m2)];

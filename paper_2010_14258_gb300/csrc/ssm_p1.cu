@@ -7,5 +7,4 @@ template cudaError_t launch_one<10, 1>(const SsmParams& p, cudaStream_t st);
 template cudaError_t launch_one<11, 1>(const SsmParams& p, cudaStream_t st);
 template cudaError_t launch_one<12, 1>(const SsmParams& p, cudaStream_t st);
 template cudaError_t launch_one<13, 1>(const SsmParams& p, cudaStream_t st);
-template cudaError_t launch_one<14, 1>(const SsmParams& p, cudaStream_t st);
 }  // namespace ldbp

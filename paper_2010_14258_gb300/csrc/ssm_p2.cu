@@ -5,5 +5,4 @@ namespace ldbp {
 template cudaError_t launch_one<11, 2>(const SsmParams& p, cudaStream_t st);
 template cudaError_t launch_one<12, 2>(const SsmParams& p, cudaStream_t st);
 template cudaError_t launch_one<13, 2>(const SsmParams& p, cudaStream_t st);
-template cudaError_t launch_one<14, 2>(const SsmParams& p, cudaStream_t st);
 }  // namespace ldbp
