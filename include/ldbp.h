@@ -92,6 +92,53 @@ int ldbp_device_status(void);
 int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
                const void* x, void* y, int64_t n, int32_t batch, void* ckpt, void* stream);
 
+/*
+ * ldbp_backward -- adjoint of ldbp_apply (hand-written reverse sweep).
+ *
+ * Given g_y = dl/dRe(y) + j dl/dIm(y) of a real loss l at the output of
+ * ldbp_apply, computes for i = M-1 .. 0 (Eq. (7) with the FIR of Sec. III-B):
+ *   Kerr:  g_v = exp(-j c_i |v|^2) g_w - 2 c_i Im(w conj(g_w)) v,  v = A_i u_i, w = u_{i+1}
+ *   taps:  dl/dh^(i)_0 = sum_{b,m} g_v conj(u_i[m]),
+ *          dl/dh^(i)_k = sum_{b,m} g_v conj(u_i[m-k] + u_i[m+k])  (k = 1..K_i)
+ *   FIR:   g_u = A_i^H g_v  (symmetric FIR with conjugated taps).
+ * v is recomputed from the checkpoints u_i written by ldbp_apply (ckpt
+ * != NULL there); the sweep is one fused kernel plus a deterministic
+ * fixed-order reduction of the per-block tap sums (bitwise reproducible).
+ *  taps, taps_stride, T, c, M  as in ldbp_apply (same values as the forward call)
+ *  ckpt       device complex64 [M][batch][n] from ldbp_apply
+ *  gy         device complex64 [batch][n]
+ *  gx         device complex64 [batch][n] (output, dl/dx) or NULL
+ *  gtaps      device complex64 [M][taps_stride] (output); entries k > K_i are 0
+ *  workspace  device scratch of at least ldbp_backward_workspace() bytes,
+ *             owned by the caller; its contents on entry are irrelevant
+ * Errors: LDBP_EINVAL (as ldbp_apply; a too small workspace; gx aliasing gy
+ * or ckpt; halo sum H + K_max too large for one tile), LDBP_ECUDA.
+ */
+int ldbp_backward(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
+                  const void* ckpt, const void* gy, void* gx, void* gtaps, int64_t n, int32_t batch, void* workspace,
+                  size_t workspace_bytes, void* stream);
+
+/* Workspace bytes ldbp_backward needs for (n, batch, T[0..M)).  Host only. */
+int ldbp_backward_workspace(int64_t n, int32_t batch, const int32_t* T, int32_t M, size_t* bytes);
+
+/*
+ * ldbp_adam_step -- one Adam update of the LDBP taps (Sec. IV-B; Table I:
+ * learning rate 1e-3) with the pruning mask of Sec. IV-C.
+ *
+ * Treats taps [M][taps_stride] complex64 as real pairs and applies, per real
+ * parameter, m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+ * theta <- theta - lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * Taps with k > K_i = (T_i - 1)/2 (pruned or unused) and their moments are
+ * set to zero, so a filter shortened by the caller stays shortened.
+ *  taps   device complex64 [M][taps_stride] (updated in place)
+ *  gtaps  device complex64 [M][taps_stride] gradient (ldbp_backward)
+ *  m, v   device float [M][taps_stride][2] moments (caller-owned, start at 0)
+ *  T      host int32 [M] current filter lengths; step >= 1.
+ * Errors: LDBP_EINVAL, LDBP_ECUDA.
+ */
+int ldbp_adam_step(void* taps, const void* gtaps, float* m, float* v, const int32_t* T, int32_t M,
+                   int32_t taps_stride, int32_t step, float lr, float beta1, float beta2, float eps, void* stream);
+
 /* Fiber parameters in the paper's units (Table I). */
 typedef struct {
   double alpha_db_per_km;   /* power attenuation, dB/km (>= 0) */

@@ -155,3 +155,67 @@ def snr_db(stats):
     """Effective SNR (Eq. (14), read as sum_b ||s_b||^2 / sum_b ||s_hat_b - s_b||^2) in dB."""
     st = stats.double().cpu()
     return float(10.0 * torch.log10(st[:, 1].sum() / st[:, 0].sum()).item())
+
+
+def ldbp_backward_workspace_bytes(n, batch, T):
+    import ctypes
+    out = ctypes.c_size_t(0)
+    _lib.check(_lib.lib().ldbp_backward_workspace(int(n), int(batch), _lib.i32_array(T), len(T), ctypes.byref(out)))
+    return out.value
+
+
+def ldbp_backward(taps, T, c, ckpt, gy, want_gx=True, workspace=None, gtaps_out=None):
+    """Adjoint of ldbp_apply: returns (gx or None, gtaps [M, stride]) for the loss gradient gy."""
+    _check_c64("gy", gy)
+    _check_c64("taps", taps)
+    B, n = gy.shape
+    M = len(T)
+    _check_c64("ckpt", ckpt, (M, B, n))
+    need = ldbp_backward_workspace_bytes(n, B, T)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 8), dtype=torch.uint8, device=gy.device)
+    gx = torch.empty_like(gy) if want_gx else None
+    gt = torch.empty_like(taps) if gtaps_out is None else gtaps_out
+    _lib.check(_lib.lib().ldbp_backward(_ptr(taps), taps.shape[1], _lib.i32_array(T), _lib.f32_array(c), M,
+                                        _ptr(ckpt), _ptr(gy), _ptr(gx), _ptr(gt), n, B, _ptr(workspace),
+                                        workspace.numel(), _stream()))
+    return gx, gt
+
+
+class LDBPFunction(torch.autograd.Function):
+    """y = LDBP(x; taps) with the hand-written adjoint (checkpoints every step).
+
+    forward(x, taps, T, c): x complex64 [B, n], taps complex64 [M, stride] (the
+    trainable half-tap vectors), T list of filter lengths, c list of Kerr
+    coefficients.  Gradients follow torch's complex convention
+    (dl/dRe + j dl/dIm), which is the library's.
+    """
+
+    @staticmethod
+    def forward(ctx, x, taps, T, c):
+        M = len(T)
+        B, n = x.shape
+        ckpt = torch.empty((M, B, n), dtype=torch.complex64, device=x.device)
+        y = ldbp_apply(taps.detach().contiguous(), list(T), list(c), x.detach().contiguous(), ckpt=ckpt)
+        ctx.save_for_backward(taps.detach().contiguous(), ckpt)
+        ctx.T, ctx.c = list(T), list(c)
+        ctx.need_x = x.requires_grad
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        taps, ckpt = ctx.saved_tensors
+        gx, gt = ldbp_backward(taps, ctx.T, ctx.c, ckpt, gy.contiguous(), want_gx=ctx.need_x)
+        return gx, gt, None, None
+
+
+def adam_step(taps, gtaps, m, v, T, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam update of taps [M, stride] with moments m, v (float32 [M, stride, 2])."""
+    _check_c64("taps", taps)
+    _check_c64("gtaps", gtaps, tuple(taps.shape))
+    M, stride = taps.shape
+    for name, t in (("m", m), ("v", v)):
+        if t.dtype != torch.float32 or tuple(t.shape) != (M, stride, 2) or not t.is_contiguous():
+            raise ValueError(f"{name} must be float32 [M, stride, 2]")
+    _lib.check(_lib.lib().ldbp_adam_step(_ptr(taps), _ptr(gtaps), _ptr(m), _ptr(v), _lib.i32_array(T), M, stride,
+                                         int(step), float(lr), float(beta1), float(beta2), float(eps), _stream()))

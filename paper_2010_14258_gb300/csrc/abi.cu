@@ -4,6 +4,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "ldbp_bwd.cuh"
 #include "ldbp_fwd.cuh"
 
 namespace ldbp {
@@ -33,8 +34,9 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 int make_tile_plan(long long n, int H, TilePlan* out) {
   const int Hp = H + (H & 1);
+  if (2 * Hp > kFwdS / 2) return -1;
   const int Lmax = kFwdS - 2 * Hp;
-  if (2 * H > kFwdS / 2 || Lmax < 2) return -1;
+  if (Lmax < 2) return -1;
   long long tpw = (n + Lmax - 1) / Lmax;
   long long L = (n + tpw - 1) / tpw;
   L += L & 1;
@@ -127,6 +129,90 @@ int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const fl
   }
   cudaError_t e = launch_ldbp_fwd(p, kmax, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "ldbp_fwd launch");
+  return LDBP_OK;
+}
+
+}  // extern "C"
+
+namespace ldbp {
+
+// Backward tile plan: halo H + K_max per side (see ldbp_bwd.cu).
+static int bwd_plan(long long n, const int32_t* T, int M, TilePlan* plan, int* kmax) {
+  int H = 0;
+  *kmax = 0;
+  for (int i = 0; i < M; ++i) {
+    const int K = (T[i] - 1) / 2;
+    H += K;
+    *kmax = K > *kmax ? K : *kmax;
+  }
+  return make_tile_plan(n, H + *kmax, plan);
+}
+
+}  // namespace ldbp
+
+extern "C" {
+
+int ldbp_backward_workspace(int64_t n, int32_t batch, const int32_t* T, int32_t M, size_t* bytes) {
+  if (!T || !bytes) return fail(LDBP_EINVAL, "T and bytes must be non-NULL");
+  if (M < 1 || M > LDBP_MAX_STEPS) return fail(LDBP_EINVAL, "M=%d outside 1..%d", M, LDBP_MAX_STEPS);
+  if (n < 1 || batch < 1) return fail(LDBP_EINVAL, "n=%lld, batch=%d must be >= 1", (long long)n, batch);
+  for (int i = 0; i < M; ++i)
+    if (T[i] < 1 || T[i] % 2 == 0 || (T[i] - 1) / 2 > LDBP_MAX_HALF_TAPS)
+      return fail(LDBP_EINVAL, "T[%d]=%d must be odd in 1..%d", i, T[i], 2 * LDBP_MAX_HALF_TAPS + 1);
+  TilePlan plan;
+  int kmax = 0;
+  if (bwd_plan(n, T, M, &plan, &kmax)) return fail(LDBP_EINVAL, "halo sum too large for one tile");
+  const int cls = fwd_kmax_class(kmax);
+  *bytes = (size_t)plan.tiles_per_wave * (size_t)batch * (size_t)M * (size_t)(cls + 1) * sizeof(float2);
+  return LDBP_OK;
+}
+
+int ldbp_backward(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
+                  const void* ckpt, const void* gy, void* gx, void* gtaps, int64_t n, int32_t batch, void* workspace,
+                  size_t workspace_bytes, void* stream) {
+  if (!ckpt || !gy || !gtaps || !workspace)
+    return fail(LDBP_EINVAL, "ckpt, gy, gtaps and workspace must be non-NULL");
+  if (n < 1 || batch < 1) return fail(LDBP_EINVAL, "n=%lld, batch=%d must be >= 1", (long long)n, batch);
+  int H = 0, kmax = 0;
+  if (int rc = check_model(taps, taps_stride, T, c, M, n, &H, &kmax)) return rc;
+  size_t need = 0;
+  if (int rc = ldbp_backward_workspace(n, batch, T, M, &need)) return rc;
+  if (workspace_bytes < need)
+    return fail(LDBP_EINVAL, "workspace of %zu bytes is smaller than the %zu bytes needed", workspace_bytes, need);
+  const size_t bytes = (size_t)n * (size_t)batch * sizeof(float2);
+  if (gx && (overlaps(gx, bytes, gy, bytes) || overlaps(gx, bytes, ckpt, bytes * M)))
+    return fail(LDBP_EINVAL, "gx overlaps gy or ckpt");
+  TilePlan plan;
+  bwd_plan(n, T, M, &plan, &kmax);
+  if ((long long)plan.tiles_per_wave * batch > 0x7fffffffLL) return fail(LDBP_EINVAL, "grid too large");
+  const int cls = fwd_kmax_class(kmax);
+  BwdParams p;
+  memset(&p, 0, sizeof(p));
+  p.ckpt = static_cast<const float2*>(ckpt);
+  p.gy = static_cast<const float2*>(gy);
+  p.gx = static_cast<float2*>(gx);
+  p.partial = static_cast<float2*>(workspace);
+  p.taps = static_cast<const float2*>(taps);
+  p.taps_stride = taps_stride;
+  p.n = n;
+  p.batch = batch;
+  p.M = M;
+  p.tiles_per_wave = plan.tiles_per_wave;
+  p.L = plan.L;
+  p.Hp = plan.Hp;
+  TapReduceK kk;
+  memset(&kk, 0, sizeof(kk));
+  for (int i = 0; i < M; ++i) {
+    p.K[i] = (T[i] - 1) / 2;
+    p.c[i] = c[i];
+    kk.K[i] = p.K[i];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = launch_ldbp_bwd(p, cls, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ldbp_bwd launch");
+  e = launch_tap_reduce(p.partial, plan.tiles_per_wave * batch, M, cls + 1, kk, static_cast<float2*>(gtaps),
+                        taps_stride, st);
+  if (e != cudaSuccess) return cuda_fail(e, "tap reduce launch");
   return LDBP_OK;
 }
 

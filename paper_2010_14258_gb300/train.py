@@ -1,0 +1,178 @@
+"""Learned-DBP training loop (Sec. IV-B/IV-C) on the library's own kernels.
+
+Per iteration, on the GPU: 16-QAM frames with a launch power drawn per frame
+from the training set (Sec. IV-B), RRC pulse shaping (ldbp_tx), the channel
+with ASE noise (ssm_forward), the LDBP forward pass with step checkpoints
+(ldbp_apply), the receiver loss and its gradient (ldbp_rx), the hand-written
+adjoint (ldbp_backward) and Adam (ldbp_adam_step).  The host only draws the
+symbol indices and powers (seeded), and keeps the pruning schedule: at
+predefined, front-loaded iterations the outermost tap pair of one filter is
+removed (Sec. IV-C, Example 2), choosing the filter whose outermost tap has
+the smallest magnitude among those above their target length.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+import synth
+from . import api, init
+
+
+@dataclasses.dataclass
+class TrainConfig:
+    batch: int = 64
+    nsym: int = 16384
+    sps: int = 2
+    rolloff: float = 0.1
+    baud: float = 10e9
+    n_spans: int = 25
+    span_km: float = 80.0
+    channel_steps: int = 100
+    ase: bool = True
+    nf_db: float = 5.0
+    powers_dbm: tuple = tuple(range(-4, 7))
+    t_start: int = 31
+    t_end: int = 3
+    iters: int = 1000
+    lr: float = 1e-3
+    prune_frac: float = 0.6
+    seed: int = 3
+    linear_only: bool = False
+
+    @property
+    def fs(self):
+        return self.baud * self.sps
+
+    @property
+    def n(self):
+        return self.nsym * self.sps
+
+
+def pruning_schedule(total_steps: int, iters: int, frac: float):
+    """Front-loaded pruning iterations floor(frac iters (j/P)^2), j = 1..P."""
+    return [int(math.floor(frac * iters * (j / total_steps) ** 2)) for j in range(1, total_steps + 1)]
+
+
+class Trainer:
+    def __init__(self, cfg: TrainConfig, fiber=None):
+        self.cfg = cfg
+        self.fiber = fiber or synth.Fiber()
+        M = cfg.n_spans
+        self.M = M
+        self.T = [cfg.t_start] * M
+        taps, c = init.ldbp_init(self.T, span_km=cfg.span_km, fs=cfg.fs, fiber=self.fiber, sps=cfg.sps,
+                                 rolloff=cfg.rolloff)
+        self.c = [0.0] * M if cfg.linear_only else [float(np.float32(ci)) for ci in c]
+        self.stride = (cfg.t_start - 1) // 2 + 1
+        arr = np.zeros((M, self.stride), np.complex64)
+        for i, h in enumerate(taps):
+            arr[i, : len(h)] = h
+        self.taps = torch.from_numpy(arr).cuda()
+        self.m = torch.zeros((M, self.stride, 2), dtype=torch.float32, device="cuda")
+        self.v = torch.zeros_like(self.m)
+        self.step_count = 0
+        steps = sum((cfg.t_start - cfg.t_end) // 2 for _ in range(M))
+        self.schedule = pruning_schedule(steps, cfg.iters, cfg.prune_frac) if steps else []
+        B, n = cfg.batch, cfg.n
+        self.ckpt = torch.empty((M, B, n), dtype=torch.complex64, device="cuda")
+        self.out = torch.empty((B, n), dtype=torch.complex64, device="cuda")
+        self.ws_rx = torch.empty((B, n), dtype=torch.complex64, device="cuda")
+        self.ws_bwd = None
+        self.history = []
+
+    # ------------------------------------------------------------------ data
+    def link(self, counter: int):
+        cfg = self.cfg
+        return synth.Link(cfg.n_spans, cfg.span_km, cfg.channel_steps, True, cfg.ase, cfg.nf_db, 1.946e14,
+                          seed=cfg.seed * 1000003 + 17, counter=counter)
+
+    def frames(self, it: int, batch=None, powers_dbm=None):
+        """Symbols (device complex64 [B, nsym]), launch powers (device float32 [B]) and received waveforms."""
+        cfg = self.cfg
+        B = batch or cfg.batch
+        s = synth.qam16_symbols(B, cfg.nsym, cfg.seed * 7919 + it).astype(np.complex64)
+        pd = synth.launch_powers_dbm(B, cfg.seed * 104729 + it, powers_dbm or cfg.powers_dbm)
+        p = (1e-3 * 10.0 ** (pd / 10.0)).astype(np.float32)
+        sd = torch.from_numpy(s).cuda()
+        pw = torch.from_numpy(p).cuda()
+        x = api.tx(sd, pw, sps=cfg.sps, rolloff=cfg.rolloff)
+        y = api.ssm_forward(self.fiber, self.link(it), cfg.fs, x, out=x)
+        return sd, pw, y
+
+    # ------------------------------------------------------------------ training
+    def train_step(self, it: int) -> float:
+        cfg = self.cfg
+        sd, pw, y = self.frames(it)
+        api.ldbp_apply(self.taps, self.T, self.c, y, ckpt=self.ckpt, out=self.out)
+        stats, _, g = api.rx(self.out, sd, pw, sps=cfg.sps, rolloff=cfg.rolloff, grad=True, workspace=self.ws_rx)
+        need = api.ldbp_backward_workspace_bytes(cfg.n, cfg.batch, self.T)
+        if self.ws_bwd is None or self.ws_bwd.numel() < need:
+            self.ws_bwd = torch.empty(need, dtype=torch.uint8, device="cuda")
+        _, gt = api.ldbp_backward(self.taps, self.T, self.c, self.ckpt, g, want_gx=False, workspace=self.ws_bwd)
+        self.step_count += 1
+        api.adam_step(self.taps, gt, self.m, self.v, self.T, self.step_count, lr=cfg.lr)
+        while self.schedule and self.schedule[0] <= it:
+            self.schedule.pop(0)
+            self.prune_one()
+        loss = float(stats[:, 0].mean().item())
+        self.history.append(loss)
+        return loss
+
+    def prune_one(self):
+        """Remove the outermost tap pair of one filter (Sec. IV-C)."""
+        h = self.taps.cpu().numpy()
+        best, mag = -1, np.inf
+        for i, T in enumerate(self.T):
+            if T > self.cfg.t_end:
+                a = abs(h[i, (T - 1) // 2])
+                if a < mag:
+                    best, mag = i, a
+        if best >= 0:
+            self.T[best] -= 2
+
+    def fit(self, iters=None, log_every=0):
+        for it in range(iters or self.cfg.iters):
+            loss = self.train_step(it)
+            if log_every and it % log_every == 0:
+                print(f"it {it:5d} loss {loss:.4e} snr {10 * np.log10(1 / loss):.2f} dB taps {sum(self.T)}")
+        return self.history
+
+    # ------------------------------------------------------------------ evaluation
+    def evaluate(self, frames: int = 4, power_dbm: float = 0.0, first_frame: int = 10_000_000):
+        """Effective SNR (dB) of LDBP, of 1-StPS FD DBP and of no compensation at one power."""
+        cfg = self.cfg
+        acc = {"ldbp": [0.0, 0.0], "dbp": [0.0, 0.0]}
+        for f in range(frames):
+            sd, pw, y = self.frames(first_frame + f, powers_dbm=(power_dbm,))
+            out = api.ldbp_apply(self.taps, self.T, self.c, y)
+            st, _, _ = api.rx(out, sd, pw, sps=cfg.sps, rolloff=cfg.rolloff)
+            z = api.dbp_apply(self.fiber, self.link(0), cfg.fs, y, steps_per_span=1, symmetric=False)
+            sd2, _, _ = api.rx(z, sd, pw, sps=cfg.sps, rolloff=cfg.rolloff)
+            for key, s in (("ldbp", st), ("dbp", sd2)):
+                s = s.double().cpu()
+                acc[key][0] += float(s[:, 1].sum())
+                acc[key][1] += float(s[:, 0].sum())
+        return {k: 10 * np.log10(a / b) for k, (a, b) in acc.items()}
+
+    # ------------------------------------------------------------------ checkpoint / resume
+    def state(self):
+        return {"taps": self.taps.cpu().numpy(), "T": np.array(self.T), "c": np.array(self.c),
+                "m": self.m.cpu().numpy(), "v": self.v.cpu().numpy(), "step": self.step_count,
+                "schedule": np.array(self.schedule, dtype=np.int64)}
+
+    def save(self, path):
+        np.savez(path, **self.state())
+
+    def load(self, path):
+        d = np.load(path)
+        self.taps.copy_(torch.from_numpy(d["taps"]))
+        self.T = [int(t) for t in d["T"]]
+        self.c = [float(x) for x in d["c"]]
+        self.m.copy_(torch.from_numpy(d["m"]))
+        self.v.copy_(torch.from_numpy(d["v"]))
+        self.step_count = int(d["step"])
+        self.schedule = [int(t) for t in d["schedule"]]

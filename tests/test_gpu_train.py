@@ -1,0 +1,79 @@
+"""Optimiser parity and the end-to-end training test: LDBP trained on the GPU
+with the library's own forward/adjoint kernels gains over its untrained
+initialisation, over the same model without nonlinear steps and over
+1-step-per-span frequency-domain DBP."""
+import numpy as np
+import pytest
+
+from oracle import train as otrain
+from tests.util import gpu_lib
+
+pytestmark = pytest.mark.gpu
+
+
+def test_adam_kernel_matches_oracle_and_masks_pruned_taps():
+    import torch
+    gpu_lib()
+    from paper_2010_14258_gb300 import api
+    rng = np.random.default_rng(0)
+    M, stride = 3, 5
+    T = [9, 5, 1]
+    theta = (rng.standard_normal((M, stride)) + 1j * rng.standard_normal((M, stride))).astype(np.complex64)
+    taps = torch.from_numpy(theta.copy()).cuda()
+    m = torch.zeros((M, stride, 2), dtype=torch.float32, device="cuda")
+    v = torch.zeros_like(m)
+    th = theta.view(np.float32).astype(np.float64).reshape(M, stride, 2)
+    mm = np.zeros_like(th)
+    vv = np.zeros_like(th)
+    for t in range(1, 6):
+        g = (rng.standard_normal((M, stride)) + 1j * rng.standard_normal((M, stride))).astype(np.complex64)
+        api.adam_step(taps, torch.from_numpy(g).cuda(), m, v, T, t, lr=1e-2)
+        gr = g.view(np.float32).astype(np.float64).reshape(M, stride, 2)
+        th, mm, vv = otrain.adam(th, gr, mm, vv, t, lr=1e-2)
+        for i, Ti in enumerate(T):  # the mask of Sec. IV-C: pruned taps are zero
+            th[i, (Ti - 1) // 2 + 1:] = 0
+            mm[i, (Ti - 1) // 2 + 1:] = 0
+            vv[i, (Ti - 1) // 2 + 1:] = 0
+    torch.cuda.synchronize()
+    out = taps.cpu().numpy().view(np.float32).reshape(M, stride, 2)
+    assert np.max(np.abs(out - th)) < 1e-5
+    assert np.all(taps.cpu().numpy()[0, 5:] == 0) and np.all(taps.cpu().numpy()[2, 1:] == 0)
+
+
+def test_training_gains_over_untrained_and_linear_only_and_dbp():
+    gpu_lib()
+    from paper_2010_14258_gb300.train import Trainer, TrainConfig
+    kw = dict(batch=16, nsym=4096, n_spans=10, channel_steps=20, powers_dbm=(4, 5, 6), t_start=9, t_end=7,
+              iters=1200, lr=3e-4, seed=1, prune_frac=0.5)
+    tr = Trainer(TrainConfig(**kw))
+    e0 = tr.evaluate(frames=2, power_dbm=5.0)
+    tr.fit()
+    e1 = tr.evaluate(frames=2, power_dbm=5.0)
+    assert tr.T == [7] * 10                      # every filter pruned 9 -> 7
+    assert e1["ldbp"] > e0["ldbp"] + 3.0         # learning gains over the LS initialisation
+    assert e1["ldbp"] > e1["dbp"] + 1.0          # and over 1-StPS FD DBP
+    lin = Trainer(TrainConfig(**dict(kw, linear_only=True, iters=600)))
+    lin.fit()
+    e2 = lin.evaluate(frames=2, power_dbm=5.0)
+    assert e1["ldbp"] > e2["ldbp"] + 10.0        # the nonlinear steps matter
+
+
+def test_checkpoint_resume_is_bit_identical(tmp_path):
+    import torch
+    gpu_lib()
+    from paper_2010_14258_gb300.train import Trainer, TrainConfig
+    kw = dict(batch=4, nsym=2048, n_spans=4, channel_steps=5, powers_dbm=(3,), t_start=9, t_end=5, iters=40,
+              lr=3e-4, seed=2)
+    a = Trainer(TrainConfig(**kw))
+    for it in range(20):
+        a.train_step(it)
+    a.save(tmp_path / "ck.npz")
+    for it in range(20, 40):
+        a.train_step(it)
+    b = Trainer(TrainConfig(**kw))
+    b.load(tmp_path / "ck.npz")
+    for it in range(20, 40):
+        b.train_step(it)
+    torch.cuda.synchronize()
+    assert a.T == b.T
+    assert np.array_equal(a.taps.cpu().numpy(), b.taps.cpu().numpy())
