@@ -121,6 +121,38 @@ int ldbp_backward(const void* taps, int32_t taps_stride, const int32_t* T, const
 /* Workspace bytes ldbp_backward needs for (n, batch, T[0..M)).  Host only. */
 int ldbp_backward_workspace(int64_t n, int32_t batch, const int32_t* T, int32_t M, size_t* bytes);
 
+/* Size of the device array ldbp_backward_static uses as scratch: 4 MiB. */
+#define LDBP_STATIC_SCRATCH_BYTES ((size_t)4 << 20)
+
+/*
+ * ldbp_backward_static -- ldbp_backward without any device allocation.
+ *
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * call cudaMalloc, for example a host application that reserves all device
+ * memory once at start-up, or a plug-in whose framework owns every device
+ * allocation and forbids new ones while it runs.  It computes exactly what
+ * ldbp_backward computes, with the same arguments minus the workspace: the
+ * per-block tap sums go to a file-scope __device__ array of
+ * LDBP_STATIC_SCRATCH_BYTES that is part of the library's device code, so
+ * every GPU that loads the library holds those 4 MiB until the process exits.
+ * The caller still provides ckpt, gy, gx and gtaps.
+ *  - Problems whose workspace (ldbp_backward_workspace) exceeds
+ *    LDBP_STATIC_SCRATCH_BYTES are rejected with LDBP_EINVAL and a message
+ *    naming both sizes; nothing is launched.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (with that device current) and caches it; make that
+ *    first call before any stream capture.  No call allocates or frees memory.
+ *  - Every call on a device shares the one array and it keeps the last call's
+ *    contents; nothing in it needs clearing, because each call writes every
+ *    element it later reads.  Calls whose executions overlap on the GPU (on
+ *    different streams, or from several host threads) race on the array and
+ *    must be serialised by the caller.
+ * Errors: as ldbp_backward, plus LDBP_EUNSUPPORTED for a device index >= 64.
+ */
+int ldbp_backward_static(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
+                         const void* ckpt, const void* gy, void* gx, void* gtaps, int64_t n, int32_t batch,
+                         void* stream);
+
 /*
  * ldbp_adam_step -- one Adam update of the LDBP taps (Sec. IV-B; Table I:
  * learning rate 1e-3) with the pruning mask of Sec. IV-C.
