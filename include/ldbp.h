@@ -93,6 +93,44 @@ int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const fl
                const void* x, void* y, int64_t n, int32_t batch, void* ckpt, void* stream);
 
 /*
+ * Ragged batches: many learned-DBP waveforms of different length n_w, step
+ * count M_w and filter lengths in ONE persistent launch (the computation of
+ * ldbp_apply per waveform).  Waveforms are packed back to back in x and y
+ * (waveform w starts at sample offset sum_{v<w} n_v); the steps of all
+ * waveforms are packed in taps [total_steps][taps_stride] (device), c
+ * [total_steps] (device float) and T [total_steps] (host, at plan creation),
+ * waveform w owning rows sum_{v<w} M_v .. + M_w - 1.
+ *
+ * ldbp_ragged_plan_create  builds the work list of (waveform, tile) items,
+ *     longest first, in plan-owned device memory (allocates; synchronous).
+ * ldbp_ragged_autotune     times candidate tile-length caps and blocks per SM
+ *     on the given buffers (synchronous, writes y) and keeps the fastest.
+ * ldbp_apply_ragged        resets the work counter and launches the
+ *     persistent kernel on `stream`.  done_ns (device uint64 [count], zeroed
+ *     by the caller) receives each waveform's completion time and start_ns
+ *     (device uint64 [1], set to UINT64_MAX by the caller) the earliest block
+ *     start, both from the GPU global timer; either may be NULL.
+ * ldbp_ragged_graph_capture / _graph_launch  capture that launch (counter
+ *     reset + kernel) for fixed buffers into a CUDA graph owned by the plan,
+ *     and replay it on `stream`.
+ * ldbp_ragged_info         total samples, total steps, work items, tile cap,
+ *     blocks per SM of the plan.
+ * The plan is bound to the device current at creation.  Errors: LDBP_EINVAL
+ * (NULL pointers, n < 1, M outside 1..LDBP_MAX_STEPS, T invalid, halo too
+ * large, overlapping x / y, wrong device), LDBP_ECUDA.
+ */
+int ldbp_ragged_plan_create(void** plan, int32_t count, const int64_t* n, const int32_t* M, const int32_t* T,
+                            int32_t taps_stride);
+int ldbp_ragged_plan_destroy(void* plan);
+int ldbp_ragged_info(const void* plan, int64_t* total_samples, int32_t* total_steps, int32_t* items,
+                     int32_t* tile_cap, int32_t* blocks_per_sm);
+int ldbp_ragged_autotune(void* plan, const void* taps, const float* c, const void* x, void* y, void* stream);
+int ldbp_apply_ragged(void* plan, const void* taps, const float* c, const void* x, void* y, uint64_t* done_ns,
+                      uint64_t* start_ns, void* stream);
+int ldbp_ragged_graph_capture(void* plan, const void* taps, const float* c, const void* x, void* y);
+int ldbp_ragged_graph_launch(void* plan, void* stream);
+
+/*
  * ldbp_backward -- adjoint of ldbp_apply (hand-written reverse sweep).
  *
  * Given g_y = dl/dRe(y) + j dl/dIm(y) of a real loss l at the output of

@@ -52,6 +52,14 @@ _SIGNATURES = {
     "ldbp_backward_workspace": (c_int, [c_int64, c_int32, P_int32, c_int32, ctypes.POINTER(ctypes.c_size_t)]),
     "ldbp_adam_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, P_int32, c_int32, c_int32, c_int32, c_float,
                                c_float, c_float, c_float, c_void_p]),
+    "ldbp_ragged_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(c_int64), P_int32,
+                                        P_int32, c_int32]),
+    "ldbp_ragged_plan_destroy": (c_int, [c_void_p]),
+    "ldbp_ragged_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), P_int32, P_int32, P_int32, P_int32]),
+    "ldbp_ragged_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ldbp_apply_ragged": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ldbp_ragged_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "ldbp_ragged_graph_launch": (c_int, [c_void_p, c_void_p]),
     "ldbp_ubench": (c_int, [c_int32, ctypes.POINTER(c_double)]),
     "ldbp_apply": (c_int, [c_void_p, c_int32, P_int32, P_float, c_int32, c_void_p, c_void_p, c_int64, c_int32,
                            c_void_p, c_void_p]),

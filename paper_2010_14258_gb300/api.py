@@ -219,3 +219,60 @@ def adam_step(taps, gtaps, m, v, T, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1
             raise ValueError(f"{name} must be float32 [M, stride, 2]")
     _lib.check(_lib.lib().ldbp_adam_step(_ptr(taps), _ptr(gtaps), _ptr(m), _ptr(v), _lib.i32_array(T), M, stride,
                                          int(step), float(lr), float(beta1), float(beta2), float(eps), _stream()))
+
+
+class RaggedPlan:
+    """Persistent one-launch learned DBP over waveforms of uneven n, M and T.
+
+    n: per-waveform lengths; T_steps: per-waveform lists of filter lengths.
+    Device buffers: x/y packed complex64 [sum n], taps complex64
+    [sum M, stride], c float32 [sum M].
+    """
+
+    def __init__(self, n, T_steps, taps_stride):
+        import ctypes
+        self.n = [int(v) for v in n]
+        self.M = [len(t) for t in T_steps]
+        self.T = [int(t) for ts in T_steps for t in ts]
+        self.stride = int(taps_stride)
+        h = ctypes.c_void_p()
+        narr = (ctypes.c_int64 * len(self.n))(*self.n)
+        _lib.check(_lib.lib().ldbp_ragged_plan_create(ctypes.byref(h), len(self.n), narr, _lib.i32_array(self.M),
+                                                      _lib.i32_array(self.T), self.stride))
+        self.handle = h
+        self.offsets = [0]
+        for v in self.n[:-1]:
+            self.offsets.append(self.offsets[-1] + v)
+
+    def info(self):
+        import ctypes
+        ts, st, it, cap, bps = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _lib.check(_lib.lib().ldbp_ragged_info(self.handle, ctypes.byref(ts), ctypes.byref(st), ctypes.byref(it),
+                                               ctypes.byref(cap), ctypes.byref(bps)))
+        return {"total_samples": ts.value, "total_steps": st.value, "items": it.value, "tile_cap": cap.value,
+                "blocks_per_sm": bps.value}
+
+    def autotune(self, taps, c, x, y):
+        _lib.check(_lib.lib().ldbp_ragged_autotune(self.handle, _ptr(taps), _ptr(c), _ptr(x), _ptr(y), _stream()))
+
+    def apply(self, taps, c, x, y, done_ns=None, start_ns=None):
+        _lib.check(_lib.lib().ldbp_apply_ragged(self.handle, _ptr(taps), _ptr(c), _ptr(x), _ptr(y), _ptr(done_ns),
+                                                _ptr(start_ns), _stream()))
+        return y
+
+    def capture(self, taps, c, x, y):
+        _lib.check(_lib.lib().ldbp_ragged_graph_capture(self.handle, _ptr(taps), _ptr(c), _ptr(x), _ptr(y)))
+
+    def replay(self):
+        _lib.check(_lib.lib().ldbp_ragged_graph_launch(self.handle, _stream()))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.check(_lib.lib().ldbp_ragged_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

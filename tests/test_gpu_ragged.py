@@ -1,0 +1,112 @@
+"""Ragged persistent launch: every waveform of an uneven batch matches the
+oracle, graph replay and autotuning do not change results, and completion
+timestamps are recorded."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ldbp as oldbp
+from paper_2010_14258_gb300 import init
+from tests.util import c64, gpu_lib, rel_l2, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def _workload(count, seed, nmin=100, nmax=30000, tchoices=(3, 5, 9, 15, 31), mmax=12):
+    rng = np.random.default_rng(seed)
+    n = [int(v) for v in rng.integers(nmin, nmax, size=count)]
+    n[0], n[1] = 1, 7                      # degenerate tiny waveforms
+    Ms = [int(v) for v in rng.integers(1, mmax + 1, size=count)]
+    Ts = [[int(rng.choice(tchoices)) for _ in range(m)] for m in Ms]
+    taps, cs = [], []
+    for w in range(count):
+        h, c = init.ldbp_init(Ts[w], span_km=80.0, fs=20e9)
+        taps.append([c64(x) for x in h])
+        cs.append([float(np.float32(v)) for v in c])
+    x = [c64(synth.gaussian_waveform(1, n[w], 1000 + w, 3e-3)[0]) for w in range(count)]
+    return n, Ts, taps, cs, x
+
+
+def _pack(Ts, taps, cs, stride):
+    rows = sum(len(t) for t in Ts)
+    arr = np.zeros((rows, stride), np.complex64)
+    c = np.zeros(rows, np.float32)
+    r = 0
+    for w in range(len(Ts)):
+        for i in range(len(Ts[w])):
+            arr[r, : len(taps[w][i])] = taps[w][i]
+            c[r] = cs[w][i]
+            r += 1
+    return arr, c
+
+
+def test_ragged_matches_oracle_per_waveform_and_graph_replay():
+    import torch
+    gpu_lib()
+    from paper_2010_14258_gb300 import api
+    n, Ts, taps, cs, x = _workload(40, 1)
+    stride = 16
+    tarr, carr = _pack(Ts, taps, cs, stride)
+    plan = api.RaggedPlan(n, Ts, stride)
+    td, cd = to_dev(tarr), torch.from_numpy(carr).cuda()
+    xd = to_dev(np.concatenate(x))
+    y = torch.zeros_like(xd)
+    done = torch.zeros(len(n), dtype=torch.int64, device="cuda")
+    start = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    plan.apply(td, cd, xd, y, done_ns=done, start_ns=start)
+    torch.cuda.synchronize()
+    yn = to_np(y)
+    off = 0
+    for w in range(len(n)):
+        ref, _ = oldbp.forward(x[w], taps[w], cs[w])
+        assert rel_l2(yn[off: off + n[w]], ref) <= 1e-4, w
+        off += n[w]
+    assert int((done > 0).sum()) == len(n)
+    # autotune and graph replay reproduce the result bit for bit
+    plan.autotune(td, cd, xd, y)
+    y2 = torch.zeros_like(xd)
+    plan.capture(td, cd, xd, y2)
+    plan.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(to_np(y2), yn)
+    info = plan.info()
+    assert info["total_samples"] == sum(n) and info["items"] >= len(n)
+    plan.close()
+
+
+def test_ragged_config_shape_sampled():
+    # the ragged workload's shape: lengths log-uniform 2^12..2^18, 5..40 spans, T in {3,5,9,15,31}
+    import torch
+    gpu_lib()
+    from paper_2010_14258_gb300 import api
+    count = 120
+    n = [int(v) for v in synth.ragged_lengths(count, 5)]
+    spans = [int(v) for v in synth.ragged_spans(count, 5)]
+    tt = [int(v) for v in synth.ragged_taps(count, 5)]
+    Ts = [[tt[w]] * spans[w] for w in range(count)]
+    stride = 16
+    hs = {T: init.ldbp_init([T], span_km=80.0, fs=20e9) for T in set(tt)}
+    rows = sum(spans)
+    tarr = np.zeros((rows, stride), np.complex64)
+    carr = np.zeros(rows, np.float32)
+    r = 0
+    for w in range(count):
+        h, c = hs[tt[w]]
+        for _ in range(spans[w]):
+            tarr[r, : len(h[0])] = h[0]
+            carr[r] = c[0]
+            r += 1
+    g = torch.Generator(device="cuda").manual_seed(0)
+    xd = torch.randn(sum(n), generator=g, device="cuda", dtype=torch.complex64) * (1e-3 ** 0.5)
+    y = torch.empty_like(xd)
+    plan = api.RaggedPlan(n, Ts, stride)
+    plan.apply(to_dev(tarr), torch.from_numpy(carr).cuda(), xd, y)
+    torch.cuda.synchronize()
+    off = np.cumsum([0] + n[:-1])
+    for w in (0, 17, 63, 119):
+        taps_w = [c64(hs[tt[w]][0][0])] * spans[w]
+        cw = [float(carr[0])] * spans[w]
+        cw = [float(np.float32(hs[tt[w]][1][0]))] * spans[w]
+        ref, _ = oldbp.forward(to_np(xd[off[w]: off[w] + n[w]]), taps_w, cw)
+        assert rel_l2(to_np(y[off[w]: off[w] + n[w]]), ref) <= 1e-4, w
+    plan.close()
