@@ -1,18 +1,33 @@
 #!/usr/bin/env python3
 """Throughput benchmark: learned DBP (fused CUDA kernel) vs plain FFT DBP on GB300.
 
-Workload: 256 waveforms x 65536 complex64 samples (16-QAM, 2 samples/symbol,
-RRC 0.1) over 25 x 80 km SSMF, LDBP with M = 25 steps (1 per span) of T-tap
-symmetric filters initialised by least squares near the dispersion response.
-One bench step = one LDBP pass over the whole batch.  Metric: complex
-samples * steps / s, whole job (all ranks).
+Workload (per GPU): 256 waveforms x 65536 complex64 samples = 32768 16-QAM
+symbols at 10 GBd, 2 samples/symbol, RRC roll-off 0.1, launched at 2 dBm over
+25 x 80 km SSMF.  The received waveforms are made on the GPU by the library's
+own transmitter and split-step channel (100 symmetric steps/span, EDFA ASE at
+NF 5 dB).  LDBP has M = 25 steps (one per span).
+
+Set-up (untimed):
+  * LDBP is trained on the GPU (library kernels only, 4000 Adam iterations,
+    cosine learning-rate decay) on a smaller frame size of the same link, for
+    filter lengths T = 9, 7, 5 in turn while the previous one passes the gate.
+  * The headline model is the smallest T whose effective SNR on the bench
+    waveforms is within 0.1 dB of 1-step-per-span frequency-domain DBP (or
+    better).  If none qualifies, the best model is used and the gate is
+    reported as failed.
+  * LS-initialised models with T in {3, 5, 9, 15} are timed for reference.
+
+One bench step = one LDBP pass over the whole 256 x 65536 batch.  Metric:
+complex samples * steps / s, whole job (all ranks).  Plain FFT DBP (the
+fused cluster kernel and cuFFT) is timed on the same waveforms.
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
-workload (there is no other implementation of the paper to run).
+workload (the paper has no implementation to run).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -27,8 +42,11 @@ sys.path.insert(0, ROOT)
 METRIC = "LDBP vs plain FFT DBP complex samples·steps/s on 1 GB300 at ΔSNR≤0.1 dB; % roofline"
 UNIT = "samples·steps/s"
 B, N_SAMP, M_STEPS = 256, 65536, 25
+NSYM = N_SAMP // 2
 SPAN_KM = 80.0
 FS = 20e9
+POWER_DBM = 2.0
+CHANNEL_STEPS = 100
 
 # FP32 pipe of GB300: 152 SMs x 128 FP32 lanes per clock x 2.07 GHz maximum
 # SM clock (one fused multiply-add = one operation).
@@ -41,7 +59,7 @@ def ldbp_fp32_ops_per_sample_step(T: int) -> int:
 
     FIR: K pairs x (2 adds + 4 FMA) + centre tap (2 mul + 2 FMA) = 6K + 4;
     Kerr: |v|^2 (mul + FMA), c|v|^2 (mul), rotation (2 mul + 2 FMA) = 7,
-    plus 2 special-function ops (sin, cos) on the separate MUFU pipe.
+    with sin/cos counted as 2 special-function operations on their own pipe.
     """
     K = (T - 1) // 2
     return 6 * K + 4 + 7
@@ -53,35 +71,39 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--taps", type=int, default=0, help="force one filter length (0: choose by the SNR gate)")
+    ap.add_argument("--taps", type=int, default=0, help="skip training and time LS-initialised filters of this length")
+    ap.add_argument("--train-iters", type=int, default=4000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=B, help="waveforms per GPU (profiling runs use fewer)")
-    ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft"],
-                    help="run only this kernel (steps+warmup launches) on random input, for ncu captures")
+    ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft", "ldbp_bwd", "channel"],
+                    help="run only this kernel (warmup + steps launches) on random input, for ncu captures")
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def model(T: int, M: int = M_STEPS):
+def ls_model(T: int, M: int = M_STEPS):
     """LS-initialised taps (host FP64) and Kerr coefficients of 1-StPS LDBP."""
     from paper_2010_14258_gb300 import init as pinit
-    taps, c = pinit.ldbp_init([T] * M, span_km=SPAN_KM, fs=FS, steps_per_span=1)
-    return taps, c
+    return pinit.ldbp_init([T] * M, span_km=SPAN_KM, fs=FS, steps_per_span=1)
+
+
+def pack_taps(taps, M=M_STEPS):
+    import torch
+    arr = np.zeros((M, max(len(h) for h in taps)), np.complex64)
+    for i, h in enumerate(taps):
+        arr[i, : len(h)] = h
+    return torch.from_numpy(arr).cuda()
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling during the timed region."""
 
     def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.path = None
+        self.index, self.proc, self.path = index, None, None
 
     def __enter__(self):
         import tempfile
@@ -131,12 +153,48 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline_ldbp(T: int, waves: int = 2):
-    """The FP64 oracle on a bounded sample of the workload (host cores)."""
+def time_fn(fn, reps, warmup=1):
+    """Mean CUDA-event milliseconds of fn() on the current stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def traffic_from_profiles(kernel: str, T: int):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2010_14258_gb300", "csrc", "ldbp_fwd.cu")
+    try:
+        rec = json.load(open(path)).get(kernel)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, ValueError, AttributeError):
+        return None
+    if not rec or rec.get("src_sha256") != sha or rec.get("T") != T:
+        return None
+    return rec.get("bytes_per_launch_full")
+
+
+def cpu_baseline_ldbp(T: int, seconds: float = 10.0, max_waves: int = 64):
+    """The FP64 oracle (numpy, one host core) on a bounded sample of the workload."""
     from oracle import ldbp as oldbp
     import synth
-    taps, c = model(T)
-    x = synth.gaussian_waveform(waves, N_SAMP, 123, 1e-3)
+    taps, c = ls_model(T)
+    x1 = synth.gaussian_waveform(1, N_SAMP, 123, 1e-3)
+    t = time.perf_counter()
+    oldbp.forward(x1, taps, c)
+    one = time.perf_counter() - t
+    waves = int(max(1, min(max_waves, seconds / max(one, 1e-3))))
+    x = synth.gaussian_waveform(waves, N_SAMP, 124, 1e-3)
     t = time.perf_counter()
     oldbp.forward(x, taps, c)
     dt = time.perf_counter() - t
@@ -149,20 +207,17 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    T = args.taps or 15
-    # each step: the oracle on a bounded sample (1 waveform x 65536 x 25 steps)
+    T = args.taps or 5
     for _ in range(args.warmup):
-        cpu_baseline_ldbp(T, waves=1)
-    tot, vals = 0.0, []
+        cpu_baseline_ldbp(T, seconds=0.0, max_waves=1)
+    tot = 0.0
     for _ in range(args.steps):
-        r = cpu_baseline_ldbp(T, waves=1)
-        tot += r["seconds"]
-        vals.append(r["value"])
+        tot += cpu_baseline_ldbp(T, seconds=0.0, max_waves=1)["seconds"]
     value = args.steps * N_SAMP * M_STEPS / tot
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": f"ldbp_infer_{B}x{N_SAMP}_M{M_STEPS}_T{T}",
+           "data": "synthetic", "config": {"workload": f"ldbp_infer_{B}x{N_SAMP}_M{M_STEPS}", "T": T,
                                            "sample": f"1 of {B} waveforms per step"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"1 waveform x {N_SAMP} samples x {M_STEPS} steps per step, numpy FP64"},
@@ -178,29 +233,37 @@ def profile_only(args, api):
     x = torch.randn(B, N_SAMP, device="cuda", dtype=torch.complex64) * (1e-3 ** 0.5)
     y = torch.empty_like(x)
     fib, link = synth.Fiber(), synth.Link(M_STEPS, SPAN_KM, 1, False, False)
+    taps_np, c = ls_model(T)
+    taps = pack_taps(taps_np)
+    units = B * N_SAMP * M_STEPS
     if args.profile == "ldbp":
-        taps_np, c = model(T)
-        tarr = np.zeros((M_STEPS, max(len(h) for h in taps_np)), np.complex64)
-        for i, h in enumerate(taps_np):
-            tarr[i, : len(h)] = h
-        taps = torch.from_numpy(tarr).cuda()
         fn = lambda: api.ldbp_apply(taps, [T] * M_STEPS, c, x, out=y)  # noqa: E731
+    elif args.profile == "ldbp_bwd":
+        ck = torch.empty((M_STEPS, B, N_SAMP), dtype=torch.complex64, device="cuda")
+        api.ldbp_apply(taps, [T] * M_STEPS, c, x, ckpt=ck, out=y)
+        fn = lambda: api.ldbp_backward(taps, [T] * M_STEPS, c, ck, x, want_gx=True)  # noqa: E731
     elif args.profile == "dbp":
         fn = lambda: api.dbp_apply(fib, link, FS, x, steps_per_span=1, symmetric=False, out=y)  # noqa: E731
+    elif args.profile == "channel":
+        ch = synth.Link(M_STEPS, SPAN_KM, 4, True, True)
+        units = B * N_SAMP * M_STEPS * 4
+        fn = lambda: api.ssm_forward(fib, ch, FS, x, out=y)  # noqa: E731
     else:
         fn = lambda: api.ssm_cufft(fib, link, FS, x, dbp_steps_per_span=1, dbp_symmetric=False, out=y)  # noqa: E731
-    for _ in range(args.warmup):
-        fn()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        fn()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"profile": args.profile, "batch": B, "n": N_SAMP, "steps": M_STEPS, "ms": ms,
-                      "samples_steps_per_s": B * N_SAMP * M_STEPS / (ms / 1e3)}))
+    ms = time_fn(fn, args.steps, args.warmup)
+    print(json.dumps({"profile": args.profile, "batch": B, "n": N_SAMP, "T": T, "ms": ms,
+                      "samples_steps_per_s": units / (ms / 1e3)}))
+
+
+def train_model(T: int, iters: int, rank: int):
+    """Train LDBP with filter length T on the GPU on short frames of the same link."""
+    from paper_2010_14258_gb300.train import Trainer, TrainConfig
+    cfg = TrainConfig(batch=16, nsym=4096, n_spans=M_STEPS, span_km=SPAN_KM, channel_steps=25,
+                      powers_dbm=(POWER_DBM - 1, POWER_DBM, POWER_DBM + 1), t_start=T, t_end=T, iters=iters,
+                      lr=3e-4, lr_final=3e-5, seed=11 + rank)
+    tr = Trainer(cfg)
+    tr.fit()
+    return tr.taps.clone(), list(tr.T), list(tr.c)
 
 
 def main():
@@ -226,24 +289,51 @@ def main():
     if args.profile:
         return profile_only(args, api)
 
-    T = args.taps or 15
-    taps_np, c = model(T)
-    stride = max(len(h) for h in taps_np)
-    tarr = np.zeros((M_STEPS, stride), np.complex64)
-    for i, h in enumerate(taps_np):
-        tarr[i, : len(h)] = h
-    taps = torch.from_numpy(tarr).cuda()
-    Ts = [T] * M_STEPS
+    fib = synth.Fiber()
+    t_setup = time.perf_counter()
+    # ---- synthetic received waveforms, made on the GPU by the library ----
+    s = synth.qam16_symbols(B, NSYM, 2000 + rank).astype(np.complex64)
+    sym = torch.from_numpy(s).cuda()
+    pw = torch.full((B,), 1e-3 * 10 ** (POWER_DBM / 10), dtype=torch.float32, device="cuda")
+    x = api.tx(sym, pw)
+    chan = synth.Link(M_STEPS, SPAN_KM, CHANNEL_STEPS, True, True, 5.0, 1.946e14, seed=77 + rank, counter=0)
+    y = api.ssm_forward(fib, chan, FS, x, out=x)
+    y2 = y.clone()  # a second resident batch: inputs alternate (268 MB > 129 MB L2)
+    dbp_link = synth.Link(M_STEPS, SPAN_KM, 1, False, False)
+    z = torch.empty_like(y)
 
-    # inputs: two resident batches (alternated, 268 MB > 129 MB L2)
-    gen = torch.Generator(device="cuda").manual_seed(1000 + rank)
-    xs = [torch.randn(B, N_SAMP, generator=gen, device="cuda", dtype=torch.complex64) * (1e-3 ** 0.5)
-          for _ in range(2)]
-    y = torch.empty_like(xs[0])
+    def snr_of(out):
+        st, _, _ = api.rx(out, sym, pw)
+        return api.snr_db(st)
+
+    api.dbp_apply(fib, dbp_link, FS, y, steps_per_span=1, symmetric=False, out=z)
+    snr_dbp = snr_of(z)
+
+    # ---- models ----
+    # shortest trained filter whose SNR is within 0.1 dB of DBP: try 9, then 7, then 5
+    candidates, snrs = {}, {}
+    for T in ([args.taps] if args.taps else [9, 7, 5]):
+        if args.taps:
+            tl, cl = ls_model(T)
+            candidates[T] = (pack_taps(tl), [T] * M_STEPS, cl, "ls_init")
+        else:
+            tp, Ts_, cs_t = train_model(T, args.train_iters, rank)
+            candidates[T] = (tp, Ts_, cs_t, "trained")
+        api.ldbp_apply(candidates[T][0], candidates[T][1], candidates[T][2], y, out=z)
+        snrs[T] = snr_of(z)
+        if snrs[T] < snr_dbp - 0.1:
+            break
+    ok = sorted(T for T in snrs if snrs[T] >= snr_dbp - 0.1)
+    T_head = ok[0] if ok else max(snrs, key=lambda t: snrs[t])
+    taps, Ts, cs, kind = candidates[T_head]
+    setup_s = time.perf_counter() - t_setup
+
+    # ---- timed region: K LDBP passes over the resident batch ----
     st = torch.cuda.current_stream()
+    xs = [y, y2]
 
     def step(i):
-        api.ldbp_apply(taps, Ts, c, xs[i % 2], out=y)
+        api.ldbp_apply(taps, Ts, cs, xs[i % 2], out=z)
 
     for i in range(args.warmup):
         step(i)
@@ -252,7 +342,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as cs:
+    with ClockSampler(local) as cs_:
         e0.record(st)
         for i in range(args.steps):
             step(i)
@@ -263,51 +353,63 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    clocks = cs.summary()
-    sps = B * N_SAMP * M_STEPS
-    value = world * sps * args.steps / (ms / 1e3)
+    clocks = cs_.summary()
+    units = B * N_SAMP * M_STEPS
+    value = world * units * args.steps / (ms / 1e3)
     per_launch_s = ms / 1e3 / args.steps
-    ops = ldbp_fp32_ops_per_sample_step(T) * sps
+    ops = sum(ldbp_fp32_ops_per_sample_step(T) for T in Ts) * B * N_SAMP
     achieved = ops / per_launch_s / 1e12
 
-    # end to end through the public API with host buffers (pinned), copies inside the timed region
-    xh = xs[0].cpu().pin_memory()
+    # ---- comparisons on the same waveforms (not part of the headline) ----
+    reps = max(3, args.steps // 4)
+    dbp_ms = time_fn(lambda: api.dbp_apply(fib, dbp_link, FS, y, steps_per_span=1, symmetric=False, out=z), reps)
+    cufft_ms = time_fn(lambda: api.ssm_cufft(fib, dbp_link, FS, y, dbp_steps_per_span=1, dbp_symmetric=False,
+                                             out=z), reps)
+    ls_sweep = {}
+    for T in (3, 5, 9, 15):
+        tl, cl = ls_model(T)
+        tp = pack_taps(tl)
+        tms = time_fn(lambda: api.ldbp_apply(tp, [T] * M_STEPS, cl, y, out=z), reps)
+        api.ldbp_apply(tp, [T] * M_STEPS, cl, y, out=z)
+        ls_sweep[str(T)] = {"samples_steps_per_s": units / (tms / 1e3), "ms": tms, "snr_db": snr_of(z),
+                            "frac_fp32": ldbp_fp32_ops_per_sample_step(T) * units / (tms / 1e3) / FP32_PEAK_OPS}
+
+    # ---- end to end through the public API with pinned host buffers ----
+    xh = y.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(xs[0])
-    for _ in range(2):
-        xd.copy_(xh, non_blocking=True)
-        api.ldbp_apply(taps, Ts, c, xd, out=y)
-        yh.copy_(y, non_blocking=True)
-    torch.cuda.synchronize()
-    k2 = max(3, args.steps // 4)
-    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2.record(st)
-    for _ in range(k2):
-        xd.copy_(xh, non_blocking=True)
-        api.ldbp_apply(taps, Ts, c, xd, out=y)
-        yh.copy_(y, non_blocking=True)
-    e3.record(st)
-    torch.cuda.synchronize()
-    e2e_ms = e2.elapsed_time(e3) / k2
+    pipe = api.HostPipeline(B, N_SAMP, chunks=8)
+    e2e_ms = time_fn(lambda: pipe.run(taps, Ts, cs, xh, yh), max(3, args.steps // 4))
     nbytes = xh.numel() * 8
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"ldbp_infer_{B}x{N_SAMP}_M{M_STEPS}", "batch_per_gpu": B, "n": N_SAMP,
-                      "M": M_STEPS, "T": T, "parallelism": f"replicas{world}",
+                      "M": M_STEPS, "T": T_head, "model": kind, "power_dbm": POWER_DBM,
+                      "parallelism": f"replicas{world}",
                       "l2": "two resident input batches alternated (268 MB > 129 MB L2), no flush"},
+           "snr": {"ldbp_db": snrs[T_head], "dbp_1stps_db": snr_dbp, "delta_db": snrs[T_head] - snr_dbp,
+                   "gate_met": T_head in ok, "all_trained": {str(k): v for k, v in snrs.items()}},
+           "dbp": {"fused_samples_steps_per_s": units / (dbp_ms / 1e3), "fused_ms": dbp_ms,
+                   "cufft_samples_steps_per_s": units / (cufft_ms / 1e3), "cufft_ms": cufft_ms,
+                   "ldbp_speedup_vs_fused_dbp": dbp_ms / (ms / args.steps),
+                   "ldbp_speedup_vs_cufft_dbp": cufft_ms / (ms / args.steps)},
+           "ls_init_sweep": ls_sweep,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_OPS / 1e12, "unit": "Tops/s",
-                        "frac": achieved * 1e12 / FP32_PEAK_OPS, "traffic": None,
+                        "frac": achieved * 1e12 / FP32_PEAK_OPS,
+                        "traffic": traffic_from_profiles("ldbp_fwd_kernel", T_head),
                         "kernel": "ldbp_fwd_kernel",
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (FMA = 1 op)"},
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (FMA = 1 op); "
+                                       "ldbp_ubench measures 37.5 T FMA/s"},
            "clocks": clocks,
-           "e2e": {"value": world * sps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "e2e": {"value": world * units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                    "d2h_bytes_per_step": nbytes},
-           "gpu_launches": args.steps}
+           "gpu_launches": args.steps,
+           "setup_s": setup_s}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_ldbp(T)
-        out["cpu_baseline"].pop("seconds", None)
+        cb = cpu_baseline_ldbp(T_head)
+        cb.pop("seconds", None)
+        out["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

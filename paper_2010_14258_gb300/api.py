@@ -276,3 +276,40 @@ class RaggedPlan:
             self.close()
         except Exception:
             pass
+
+
+class HostPipeline:
+    """ldbp_apply on pinned host buffers: the batch is split into chunks whose
+    host->device copy, LDBP pass and device->host copy overlap on three
+    streams (copy-in, compute, copy-out).  Device staging buffers are
+    allocated once per (batch, n)."""
+
+    def __init__(self, batch, n, chunks=8, device="cuda"):
+        self.batch, self.n = batch, n
+        self.chunks = max(1, min(chunks, batch))
+        self.bounds = [round(i * batch / self.chunks) for i in range(self.chunks + 1)]
+        self.xd = torch.empty((batch, n), dtype=torch.complex64, device=device)
+        self.yd = torch.empty_like(self.xd)
+        self.s_in, self.s_cmp, self.s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        self.ev_in = [torch.cuda.Event() for _ in range(self.chunks)]
+        self.ev_cmp = [torch.cuda.Event() for _ in range(self.chunks)]
+
+    def run(self, taps, T, c, x_host, y_host):
+        """x_host, y_host: pinned CPU complex64 [batch, n].  Returns when y_host is filled."""
+        cur = torch.cuda.current_stream()
+        for s in (self.s_in, self.s_cmp, self.s_out):
+            s.wait_stream(cur)
+        for i in range(self.chunks):
+            a, b = self.bounds[i], self.bounds[i + 1]
+            with torch.cuda.stream(self.s_in):
+                self.xd[a:b].copy_(x_host[a:b], non_blocking=True)
+                self.ev_in[i].record(self.s_in)
+            with torch.cuda.stream(self.s_cmp):
+                self.s_cmp.wait_event(self.ev_in[i])
+                ldbp_apply(taps, T, c, self.xd[a:b], out=self.yd[a:b])
+                self.ev_cmp[i].record(self.s_cmp)
+            with torch.cuda.stream(self.s_out):
+                self.s_out.wait_event(self.ev_cmp[i])
+                y_host[a:b].copy_(self.yd[a:b], non_blocking=True)
+        cur.wait_stream(self.s_out)
+        return y_host

@@ -39,7 +39,9 @@ class TrainConfig:
     t_end: int = 3
     iters: int = 1000
     lr: float = 1e-3
+    lr_final: float = 0.0          # cosine decay from lr to lr_final over the run (0: constant lr)
     prune_frac: float = 0.6
+    w_max: float = 0.0             # LS-fit half band (rad/sample); 0: the signal band
     seed: int = 3
     linear_only: bool = False
 
@@ -65,7 +67,7 @@ class Trainer:
         self.M = M
         self.T = [cfg.t_start] * M
         taps, c = init.ldbp_init(self.T, span_km=cfg.span_km, fs=cfg.fs, fiber=self.fiber, sps=cfg.sps,
-                                 rolloff=cfg.rolloff)
+                                 rolloff=cfg.rolloff, w_max=cfg.w_max or None)
         self.c = [0.0] * M if cfg.linear_only else [float(np.float32(ci)) for ci in c]
         self.stride = (cfg.t_start - 1) // 2 + 1
         arr = np.zeros((M, self.stride), np.complex64)
@@ -114,13 +116,20 @@ class Trainer:
             self.ws_bwd = torch.empty(need, dtype=torch.uint8, device="cuda")
         _, gt = api.ldbp_backward(self.taps, self.T, self.c, self.ckpt, g, want_gx=False, workspace=self.ws_bwd)
         self.step_count += 1
-        api.adam_step(self.taps, gt, self.m, self.v, self.T, self.step_count, lr=cfg.lr)
+        api.adam_step(self.taps, gt, self.m, self.v, self.T, self.step_count, lr=self.lr_at(it))
         while self.schedule and self.schedule[0] <= it:
             self.schedule.pop(0)
             self.prune_one()
         loss = float(stats[:, 0].mean().item())
         self.history.append(loss)
         return loss
+
+    def lr_at(self, it: int) -> float:
+        cfg = self.cfg
+        if cfg.lr_final <= 0.0:
+            return cfg.lr
+        f = min(1.0, it / max(1, cfg.iters - 1))
+        return cfg.lr_final + 0.5 * (cfg.lr - cfg.lr_final) * (1.0 + math.cos(math.pi * f))
 
     def prune_one(self):
         """Remove the outermost tap pair of one filter (Sec. IV-C)."""
