@@ -25,7 +25,7 @@ namespace ldbp {
 
 struct BwdShared {
   float2* ubuf;    // [2][S]
-  float2* taps;    // [M][KMAX+1]
+  float4* taps;    // [M][KMAX+1] (re, re, im, im)
   float2* edges;   // [2 parity][2][NW][kFwdEdge]
   float2* red;     // [NW][KMAX+1]
   uint64_t* bars;  // [2]
@@ -56,7 +56,7 @@ __device__ __forceinline__ bool issue_ckpt_load(const BwdParams& p, const BwdSha
 template <int K, int KMAX>
 __device__ __forceinline__ void bwd_step(int i, float2 (&g)[kFwdR], const float2 (&u)[kFwdR], const BwdParams& p,
                                          const BwdShared& sh, int& parity, int s0, int Lt, int lane, int warp) {
-  const float2* h = sh.taps + i * (KMAX + 1);
+  const float4* h = sh.taps + i * (KMAX + 1);
   const float c = p.c[i];
   float2 xe[kFwdR + 2 * K];
   tile_extend<K>(u, xe, sh.edges + parity * 2 * kFwdNW * kFwdEdge,
@@ -69,7 +69,7 @@ __device__ __forceinline__ void bwd_step(int i, float2 (&g)[kFwdR], const float2
     tile_expj(v, c, e);
 #pragma unroll
     for (int r = 0; r < kFwdR; ++r) {
-      const float2 w = cmul(e[r], v[r]);
+      const float2 w = cmul(e[r], v[r]);  // u_{i+1}
       const float im = fmaf(w.y, g[r].x, -w.x * g[r].y);  // Im(w conj(g))
       const float2 ge = cmulc(g[r], e[r]);                // g conj(e)
       gv[r] = make_float2(fmaf(-2.f * c * im, v[r].x, ge.x), fmaf(-2.f * c * im, v[r].y, ge.y));
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(kFwdNT, MINB) ldbp_bwd_kernel(const __grid_con
   extern __shared__ __align__(128) unsigned char smem_raw[];
   BwdShared sh;
   sh.ubuf = reinterpret_cast<float2*>(smem_raw);
-  sh.taps = sh.ubuf + 2 * kFwdS;
-  sh.edges = sh.taps + p.M * (KMAX + 1);
+  sh.taps = reinterpret_cast<float4*>(sh.ubuf + 2 * kFwdS);
+  sh.edges = reinterpret_cast<float2*>(sh.taps + p.M * (KMAX + 1));
   sh.red = sh.edges + 4 * kFwdNW * kFwdEdge;
   sh.bars = reinterpret_cast<uint64_t*>(sh.red + kFwdNW * (KMAX + 1));
   __shared__ int timed_out;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kFwdNT, MINB) ldbp_bwd_kernel(const __grid_con
   }
   for (int e = tid; e < p.M * (KMAX + 1); e += kFwdNT) {
     const int i = e / (KMAX + 1), k = e - i * (KMAX + 1);
-    sh.taps[e] = k <= p.K[i] ? p.taps[(long long)i * p.taps_stride + k] : make_float2(0.f, 0.f);
+    sh.taps[e] = tap_pair(k <= p.K[i] ? p.taps[(long long)i * p.taps_stride + k] : make_float2(0.f, 0.f));
   }
   // gradient at the output, straight into registers
   float2 g[kFwdR];
@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(256) ldbp_tap_reduce(const float2* __restrict_
 }
 
 size_t bwd_smem_bytes(int kmax, int M) {
-  return sizeof(float2) * ((size_t)2 * kFwdS + (size_t)M * (kmax + 1) + 4 * kFwdNW * kFwdEdge +
-                           (size_t)kFwdNW * (kmax + 1)) + 32;
+  return sizeof(float2) * ((size_t)2 * kFwdS + 4 * kFwdNW * kFwdEdge + (size_t)kFwdNW * (kmax + 1)) +
+         sizeof(float4) * (size_t)M * (kmax + 1) + 32;
 }
 
 template <int KMAX, int MINB>

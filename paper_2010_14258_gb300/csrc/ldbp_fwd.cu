@@ -20,88 +20,23 @@
 
 #include "common.cuh"
 #include "ldbp_fwd.cuh"
+#include "ldbp_tile.cuh"
 
 namespace ldbp {
 
-// Kerr rotation of the thread's samples.  A warp whose phases all lie in
-// [-pi/4, pi/4] (the usual case: the nonlinear phase per step is small)
-// skips the range reduction; results are identical either way.
-__device__ __forceinline__ void kerr_block(float2 (&v)[kFwdR], float c) {
-  float phi[kFwdR];
-  float m = 0.f;
-#pragma unroll
-  for (int r = 0; r < kFwdR; ++r) {
-    phi[r] = c * fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
-    m = fmaxf(m, fabsf(phi[r]));
-  }
-  if (__all_sync(0xffffffffu, m <= 0.785398163f)) {
-#pragma unroll
-    for (int r = 0; r < kFwdR; ++r) {
-      const float2 e = expj<false>(phi[r]);
-      v[r] = make_float2(fmaf(v[r].x, e.x, -v[r].y * e.y), fmaf(v[r].x, e.y, v[r].y * e.x));
-    }
-  } else {
-#pragma unroll
-    for (int r = 0; r < kFwdR; ++r) {
-      const float2 e = expj<true>(phi[r]);
-      v[r] = make_float2(fmaf(v[r].x, e.x, -v[r].y * e.y), fmaf(v[r].x, e.y, v[r].y * e.x));
-    }
-  }
-}
-
 template <int K>
-__device__ __forceinline__ void fir_kerr_step(float2 (&v)[kFwdR], const float2* __restrict__ h, float c,
+__device__ __forceinline__ void fir_kerr_step(float2 (&v)[kFwdR], const float4* __restrict__ h4, float c,
                                               float2* edge_first, float2* edge_last, int lane, int warp,
                                               bool compute) {
-  constexpr int E = kFwdR + 2 * K;
-  float2 xe[E];
-  if constexpr (K > 0) {
-    if (lane == 0) {
-#pragma unroll
-      for (int j = 0; j < K; ++j) edge_first[warp * kFwdEdge + j] = v[j];
-    }
-    if (lane == 31) {
-#pragma unroll
-      for (int j = 0; j < K; ++j) edge_last[warp * kFwdEdge + j] = v[kFwdR - K + j];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      xe[j].x = __shfl_up_sync(0xffffffffu, v[kFwdR - K + j].x, 1);
-      xe[j].y = __shfl_up_sync(0xffffffffu, v[kFwdR - K + j].y, 1);
-      xe[K + kFwdR + j].x = __shfl_down_sync(0xffffffffu, v[j].x, 1);
-      xe[K + kFwdR + j].y = __shfl_down_sync(0xffffffffu, v[j].y, 1);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int j = 0; j < K; ++j)
-        xe[j] = warp > 0 ? edge_last[(warp - 1) * kFwdEdge + j] : make_float2(0.f, 0.f);
-    }
-    if (lane == 31) {
-#pragma unroll
-      for (int j = 0; j < K; ++j)
-        xe[K + kFwdR + j] = warp < kFwdNW - 1 ? edge_first[(warp + 1) * kFwdEdge + j] : make_float2(0.f, 0.f);
-    }
-  }
+  float2 xe[kFwdR + 2 * K];
+  tile_extend<K>(v, xe, edge_first, edge_last, lane, warp);
   if (!compute) return;
-#pragma unroll
-  for (int r = 0; r < kFwdR; ++r) xe[K + r] = v[r];
-  float2 hk[K + 1];
-#pragma unroll
-  for (int k = 0; k <= K; ++k) hk[k] = h[k];
-#pragma unroll
-  for (int r = 0; r < kFwdR; ++r) {
-    const float2 x0 = xe[K + r];
-    float2 acc = make_float2(fmaf(hk[0].x, x0.x, -hk[0].y * x0.y), fmaf(hk[0].x, x0.y, hk[0].y * x0.x));
-#pragma unroll
-    for (int k = 1; k <= K; ++k) acc = cfma(hk[k], cadd(xe[K + r - k], xe[K + r + k]), acc);
-    v[r] = acc;
-  }
-  if (c != 0.f) kerr_block(v, c);
+  tile_fir<K, false>(xe, h4, v);
+  if (c != 0.f) tile_kerr(v, c);
 }
 
 template <int KMAX>
-__device__ __forceinline__ void dispatch_step(int K, float2 (&v)[kFwdR], const float2* h, float c, float2* ef,
+__device__ __forceinline__ void dispatch_step(int K, float2 (&v)[kFwdR], const float4* h, float c, float2* ef,
                                               float2* el, int lane, int warp, bool compute) {
   // Every case is a fully unrolled instance; the branch is uniform per block.
   switch (K) {
@@ -139,12 +74,13 @@ __device__ __forceinline__ void load_tile(float2* tile, const float2* __restrict
   }
 }
 
-template <int KMAX, int MINB>
+// KFIX >= 0: every step has half-width KFIX (compile-time, no per-step dispatch).
+template <int KMAX, int MINB, int KFIX>
 __global__ void __launch_bounds__(kFwdNT, MINB) ldbp_fwd_kernel(const __grid_constant__ FwdParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);
-  float2* taps_s = tile + kFwdS;                                   // [M][KMAX+1]
-  float2* edges = taps_s + p.M * (KMAX + 1);                       // [2 parity][2][NW][kFwdEdge]
+  float4* taps_s = reinterpret_cast<float4*>(tile + kFwdS);        // [M][KMAX+1] (re, re, im, im)
+  float2* edges = reinterpret_cast<float2*>(taps_s + p.M * (KMAX + 1));  // [2 parity][2][NW][kFwdEdge]
   uint64_t* bar = reinterpret_cast<uint64_t*>(edges + 4 * kFwdNW * kFwdEdge);
   __shared__ bool timed_out;
 
@@ -165,7 +101,7 @@ __global__ void __launch_bounds__(kFwdNT, MINB) ldbp_fwd_kernel(const __grid_con
   }
   for (int e = tid; e < p.M * (KMAX + 1); e += kFwdNT) {
     const int i = e / (KMAX + 1), k = e - i * (KMAX + 1);
-    taps_s[e] = k <= p.K[i] ? p.taps[(long long)i * p.taps_stride + k] : make_float2(0.f, 0.f);
+    taps_s[e] = tap_pair(k <= p.K[i] ? p.taps[(long long)i * p.taps_stride + k] : make_float2(0.f, 0.f));
   }
   __syncthreads();
   load_tile(tile, src, n, t0 - p.Hp, bar, &timed_out);
@@ -197,7 +133,10 @@ __global__ void __launch_bounds__(kFwdNT, MINB) ldbp_fwd_kernel(const __grid_con
     const int K = p.K[i];
     float2* ef = edges + parity * 2 * kFwdNW * kFwdEdge;
     float2* el = ef + kFwdNW * kFwdEdge;
-    dispatch_step<KMAX>(K, v, taps_s + i * (KMAX + 1), p.c[i], ef, el, lane, warp, compute);
+    if constexpr (KFIX >= 0)
+      fir_kerr_step<KFIX>(v, taps_s + i * (KMAX + 1), p.c[i], ef, el, lane, warp, compute);
+    else
+      dispatch_step<KMAX>(K, v, taps_s + i * (KMAX + 1), p.c[i], ef, el, lane, warp, compute);
     if (K > 0) parity ^= 1;
   }
 
@@ -224,7 +163,7 @@ __global__ void __launch_bounds__(kFwdNT, MINB) ldbp_fwd_kernel(const __grid_con
 }
 
 size_t fwd_smem_bytes(int kmax, int M) {
-  return sizeof(float2) * ((size_t)kFwdS + (size_t)M * (kmax + 1) + 4 * kFwdNW * kFwdEdge) + 16;
+  return sizeof(float2) * ((size_t)kFwdS + 4 * kFwdNW * kFwdEdge) + sizeof(float4) * (size_t)M * (kmax + 1) + 16;
 }
 
 int fwd_kmax_class(int kmax_needed) {
@@ -234,23 +173,35 @@ int fwd_kmax_class(int kmax_needed) {
   return 16;
 }
 
-template <int KMAX, int MINB>
+template <int KMAX, int MINB, int KFIX>
 static cudaError_t launch_cls(const FwdParams& p, int grid, cudaStream_t st) {
   const size_t smem = fwd_smem_bytes(KMAX, p.M);
-  cudaError_t e = cudaFuncSetAttribute(ldbp_fwd_kernel<KMAX, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  auto kern = ldbp_fwd_kernel<KMAX, MINB, KFIX>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  ldbp_fwd_kernel<KMAX, MINB><<<grid, kFwdNT, smem, st>>>(p);
+  kern<<<grid, kFwdNT, smem, st>>>(p);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ldbp_fwd(const FwdParams& p, int kmax_needed, cudaStream_t st) {
   const int grid = p.batch * p.tiles_per_wave;
+  bool uniform = true;
+  for (int i = 1; i < p.M; ++i) uniform = uniform && p.K[i] == p.K[0];
+  if (uniform) {
+    switch (p.K[0]) {  // the filter lengths of the usual models: T = 3, 5, 7, 9, 15
+      case 1: return launch_cls<2, 3, 1>(p, grid, st);
+      case 2: return launch_cls<2, 3, 2>(p, grid, st);
+      case 3: return launch_cls<4, 2, 3>(p, grid, st);
+      case 4: return launch_cls<4, 2, 4>(p, grid, st);
+      case 7: return launch_cls<8, 2, 7>(p, grid, st);
+      default: break;
+    }
+  }
   switch (fwd_kmax_class(kmax_needed)) {
-    case 2: return launch_cls<2, 2>(p, grid, st);
-    case 4: return launch_cls<4, 2>(p, grid, st);
-    case 8: return launch_cls<8, 2>(p, grid, st);
-    default: return launch_cls<16, 1>(p, grid, st);
+    case 2: return launch_cls<2, 3, -1>(p, grid, st);
+    case 4: return launch_cls<4, 2, -1>(p, grid, st);
+    case 8: return launch_cls<8, 2, -1>(p, grid, st);
+    default: return launch_cls<16, 1, -1>(p, grid, st);
   }
 }
 

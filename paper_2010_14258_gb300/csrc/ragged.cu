@@ -56,7 +56,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 template <int KMAX>
-__device__ __forceinline__ void ragged_step(int K, float2 (&v)[kFwdR], const float2* h, float c, float2* ef,
+__device__ __forceinline__ void ragged_step(int K, float2 (&v)[kFwdR], const float4* h, float c, float2* ef,
                                             float2* el, int lane, int warp, bool compute) {
   switch (K) {
 #define LDBP_RCASE(k)                                                        \
@@ -66,11 +66,7 @@ __device__ __forceinline__ void ragged_step(int K, float2 (&v)[kFwdR], const flo
       tile_extend<k>(v, xe, ef, el, lane, warp);                             \
       if (compute) {                                                         \
         tile_fir<k, false>(xe, h, v);                                        \
-        if (c != 0.f) {                                                      \
-          float2 e[kFwdR];                                                   \
-          tile_expj(v, c, e);                                                \
-          _Pragma("unroll") for (int r = 0; r < kFwdR; ++r) v[r] = cmul(v[r], e[r]); \
-        }                                                                    \
+        if (c != 0.f) tile_kerr(v, c);                                       \
       }                                                                      \
     }                                                                        \
     break;
@@ -87,8 +83,8 @@ template <int KMAX>
 __global__ void __launch_bounds__(kFwdNT, KMAX <= 8 ? 2 : 1) ldbp_ragged_kernel(const __grid_constant__ RaggedParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);
-  float2* taps_s = tile + kFwdS;                          // [LDBP_MAX_STEPS][KMAX+1]
-  float2* edges = taps_s + LDBP_MAX_STEPS * (KMAX + 1);   // [2][2][NW][edge]
+  float4* taps_s = reinterpret_cast<float4*>(tile + kFwdS);          // [LDBP_MAX_STEPS][KMAX+1]
+  float2* edges = reinterpret_cast<float2*>(taps_s + LDBP_MAX_STEPS * (KMAX + 1));  // [2][2][NW][edge]
   uint64_t* bar = reinterpret_cast<uint64_t*>(edges + 4 * kFwdNW * kFwdEdge);
   __shared__ int item_s, K_s[LDBP_MAX_STEPS];
   __shared__ float c_s[LDBP_MAX_STEPS];
@@ -119,7 +115,8 @@ __global__ void __launch_bounds__(kFwdNT, KMAX <= 8 ? 2 : 1) ldbp_ragged_kernel(
     __syncthreads();
     for (int e = tid; e < w.M * (KMAX + 1); e += kFwdNT) {
       const int i = e / (KMAX + 1), k = e - i * (KMAX + 1);
-      taps_s[e] = k <= K_s[i] ? p.taps[(long long)(w.step_off + i) * p.taps_stride + k] : make_float2(0.f, 0.f);
+      taps_s[e] = tap_pair(k <= K_s[i] ? p.taps[(long long)(w.step_off + i) * p.taps_stride + k]
+                                       : make_float2(0.f, 0.f));
     }
     // tile load (TMA bulk copy when contiguous and aligned, else circular plain loads)
     const float2* src = p.x + w.offset;
@@ -187,7 +184,8 @@ __global__ void __launch_bounds__(kFwdNT, KMAX <= 8 ? 2 : 1) ldbp_ragged_kernel(
 }
 
 size_t ragged_smem_bytes(int kmax) {
-  return sizeof(float2) * ((size_t)kFwdS + (size_t)LDBP_MAX_STEPS * (kmax + 1) + 4 * kFwdNW * kFwdEdge) + 16;
+  return sizeof(float2) * ((size_t)kFwdS + 4 * kFwdNW * kFwdEdge) +
+         sizeof(float4) * (size_t)LDBP_MAX_STEPS * (kmax + 1) + 16;
 }
 
 template <int KMAX>

@@ -67,13 +67,28 @@ CASES = [
 ]
 
 
+def fp32_floor(x, taps, c, trials=2, seed=0):
+    """Relative change of the FP64 forward output when x is perturbed at FP32
+    rounding level: the error floor of any FP32 evaluation of this cascade.
+    25 steps of 3-tap LS filters (in-band gain up to 1.1 per step) raise it
+    above 1e-4; well-conditioned cascades stay near 1e-7."""
+    rng = np.random.default_rng(seed)
+    ref, _ = oldbp.forward(x, taps, c)
+    worst = 0.0
+    for _ in range(trials):
+        xp = x * (1 + 6e-8 * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape)))
+        yp, _ = oldbp.forward(xp, taps, c)
+        worst = max(worst, rel_l2(yp, ref))
+    return ref, worst
+
+
 @pytest.mark.parametrize("Ts,B,n,pw", CASES)
 def test_ldbp_forward_parity(Ts, B, n, pw):
     taps, c = _model(Ts, seed=len(Ts) * 7 + n)
     x = _signal(B, n, n, pw)
     y, _ = _run(taps, Ts, c, x)
-    ref, _ = oldbp.forward(x, taps, c)
-    assert rel_l2(y, ref) <= 1e-4
+    ref, floor = fp32_floor(x, taps, c)
+    assert rel_l2(y, ref) <= max(1e-4, 10 * floor)
 
 
 @pytest.mark.parametrize("n", [1, 2, 7, 64, 511, 4096, 4097])
@@ -128,5 +143,5 @@ def test_full_size_sampled():
     torch.cuda.synchronize()
     for b in (0, 77, 255):
         xb = to_np(xd[b])
-        ref, _ = oldbp.forward(xb, taps, c)
-        assert rel_l2(to_np(y[b]), ref) <= 1e-4
+        ref, floor = fp32_floor(xb, taps, c)
+        assert rel_l2(to_np(y[b]), ref) <= max(1e-4, 10 * floor)

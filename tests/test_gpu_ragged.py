@@ -62,13 +62,18 @@ def test_ragged_matches_oracle_per_waveform_and_graph_replay():
         assert rel_l2(yn[off: off + n[w]], ref) <= 1e-4, w
         off += n[w]
     assert int((done > 0).sum()) == len(n)
-    # autotune and graph replay reproduce the result bit for bit
+    # after autotuning (which may change the tiling, and with it the
+    # per-warp choice of Kerr polynomial: results agree to FP32 rounding),
+    # a graph replay reproduces a direct launch of the same plan bit for bit
     plan.autotune(td, cd, xd, y)
+    y1 = torch.zeros_like(xd)
+    plan.apply(td, cd, xd, y1)
     y2 = torch.zeros_like(xd)
     plan.capture(td, cd, xd, y2)
     plan.replay()
     torch.cuda.synchronize()
-    assert np.array_equal(to_np(y2), yn)
+    assert np.array_equal(to_np(y2), to_np(y1))
+    assert rel_l2(to_np(y1), yn) <= 1e-6
     info = plan.info()
     assert info["total_samples"] == sum(n) and info["items"] >= len(n)
     plan.close()
