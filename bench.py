@@ -343,11 +343,13 @@ def main():
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as cs_:
+        torch.cuda.nvtx.range_push("timed")
         e0.record(st)
         for i in range(args.steps):
             step(i)
         e1.record(st)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     if world > 1:
         t = torch.tensor([ms], device="cuda")

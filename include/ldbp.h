@@ -334,7 +334,8 @@ int ldbp_rx(const void* y, const void* symbols, const float* power_w, int32_t sp
  * independent dependency chains per thread:
  *   kind 0: scalar FP32 fused multiply-add (lane operations/s),
  *   kind 1: packed FP32x2 fused multiply-add (lane FP32 operations/s, 2 per lane),
- *   kind 2: special-function sine (__sinf, operations/s).
+ *   kind 2: special-function sine (__sinf, operations/s),
+ *   kind 3: packed and scalar FP32 FMA interleaved (lane FP32 operations/s).
  * These are the denominators the fused kernels' FP32 roofline is checked
  * against (the paper itself has no hardware figures).  Allocates a 1 KB
  * scratch buffer and synchronises the device.
