@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=B, help="waveforms per GPU (profiling runs use fewer)")
     ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft", "ldbp_bwd", "channel"],
                     help="run only this kernel (warmup + steps launches) on random input, for ncu captures")
+    ap.add_argument("--workload", default="ldbp", choices=["ldbp", "channel", "ragged", "train"],
+                    help="ldbp: the headline; channel / ragged / train: the other workloads, reported separately")
     return ap.parse_args()
 
 
@@ -255,6 +257,126 @@ def profile_only(args, api):
                       "samples_steps_per_s": units / (ms / 1e3)}))
 
 
+def workload_channel(args, api):
+    """Channel data generation at scale: 128 x 2^17 samples, 32 GBd 16-QAM at 4 samples/symbol,
+    10 x 100 km, 200 symmetric steps/span, ASE; fused kernel vs cuFFT; FP32 error vs the FP64
+    oracle on sampled waveforms (one span, to bound the oracle's time)."""
+    import torch
+    import synth
+    from oracle import nlse
+    Bc, nsym, sps, fs = 128, 32768, 4, 128e9
+    fib = synth.Fiber()
+    link = synth.Link(10, 100.0, 200, True, True, 5.0, 1.946e14, seed=4, counter=0)
+    s = torch.from_numpy(synth.qam16_symbols(Bc, nsym, 4).astype(np.complex64)).cuda()
+    pw = torch.full((Bc,), 1e-3, dtype=torch.float32, device="cuda")
+    x = api.tx(s, pw, sps=sps)
+    y = torch.empty_like(x)
+    units = Bc * nsym * sps * 10 * 200
+    fused = time_fn(lambda: api.ssm_forward(fib, link, fs, x, out=y), 2)
+    cufft = time_fn(lambda: api.ssm_cufft(fib, link, fs, x, out=y), 2)
+    # FP32 vs FP64 on two sampled waveforms over one span (200 steps, no ASE), bounding the oracle's time
+    one_span = synth.Link(1, 100.0, 200, True, False)
+    errs = []
+    for b in (0, 64):
+        xb = x[b: b + 1].contiguous()
+        ref = nlse.channel(xb.cpu().numpy().astype(np.complex128), fib, one_span, fs)
+        yb = api.ssm_forward(fib, one_span, fs, xb)
+        errs.append(float(np.linalg.norm(yb.cpu().numpy() - ref) / np.linalg.norm(ref)))
+    print(json.dumps({"workload": "channel_128x131072_10x100km_200stps", "unit": UNIT,
+                      "fused_samples_steps_per_s": units / (fused / 1e3), "fused_ms": fused,
+                      "cufft_samples_steps_per_s": units / (cufft / 1e3), "cufft_ms": cufft,
+                      "speedup_vs_cufft": cufft / fused,
+                      "fp32_rel_l2_vs_fp64_per_waveform_1span_200steps": errs}))
+
+
+def workload_ragged(args, api):
+    """1000 LDBP waveforms, n log-uniform 2^12..2^18, 5..40 spans (1 step each), T in {3,5,9,15,31}:
+    one persistent launch (autotuned, graph-replayed) vs one ldbp_apply launch per waveform."""
+    import torch
+    import synth
+    from paper_2010_14258_gb300 import init as pinit
+    count = 1000
+    n = [int(v) for v in synth.ragged_lengths(count, 5)]
+    spans = [int(v) for v in synth.ragged_spans(count, 5)]
+    tt = [int(v) for v in synth.ragged_taps(count, 5)]
+    stride = 16
+    models = {T: pinit.ldbp_init([T], span_km=SPAN_KM, fs=FS) for T in set(tt)}
+    rows = sum(spans)
+    tarr = np.zeros((rows, stride), np.complex64)
+    carr = np.zeros(rows, np.float32)
+    r = 0
+    for w in range(count):
+        h, c = models[tt[w]]
+        tarr[r: r + spans[w], : len(h[0])] = h[0]
+        carr[r: r + spans[w]] = c[0]
+        r += spans[w]
+    taps, cd = torch.from_numpy(tarr).cuda(), torch.from_numpy(carr).cuda()
+    x = torch.randn(sum(n), device="cuda", dtype=torch.complex64) * (1e-3 ** 0.5)
+    y = torch.empty_like(x)
+    plan = api.RaggedPlan(n, [[tt[w]] * spans[w] for w in range(count)], stride)
+    plan.autotune(taps, cd, x, y)
+    plan.capture(taps, cd, x, y)
+    units = sum(n[w] * spans[w] for w in range(count))
+    graph_ms = time_fn(plan.replay, 10, 2)
+    done = torch.zeros(count, dtype=torch.int64, device="cuda")
+    start = torch.full((1,), 2 ** 63 - 1, dtype=torch.int64, device="cuda")
+    plan.apply(taps, cd, x, y, done_ns=done, start_ns=start)
+    torch.cuda.synchronize()
+    lat = (done - start).double().cpu().numpy() / 1e6
+    # per-waveform launches
+    off = np.cumsum([0] + n[:-1])
+    rs = np.cumsum([0] + spans[:-1])
+    per = []
+    for w in range(count):
+        Ts = [tt[w]] * spans[w]
+        per.append((taps[rs[w]: rs[w] + spans[w]], Ts, carr[rs[w]: rs[w] + spans[w]].tolist(),
+                    x[off[w]: off[w] + n[w]].view(1, -1), y[off[w]: off[w] + n[w]].view(1, -1)))
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(count + 1)]
+
+    def per_wave():
+        evs[0].record()
+        for w, (tp, Ts, cl, xw, yw) in enumerate(per):
+            api.ldbp_apply(tp, Ts, cl, xw, out=yw)
+            evs[w + 1].record()
+
+    per_wave()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per_wave()
+    torch.cuda.synchronize()
+    per_ms = evs[0].elapsed_time(evs[-1])
+    plat = np.array([evs[0].elapsed_time(evs[w + 1]) for w in range(count)])
+    info = plan.info()
+    print(json.dumps({"workload": "ragged_1000_lengths_2^12-2^18_spans_5-40_T_3-31", "unit": UNIT,
+                      "persistent_graph_samples_steps_per_s": units / (graph_ms / 1e3), "persistent_ms": graph_ms,
+                      "persistent_latency_ms_p50": float(np.percentile(lat, 50)),
+                      "persistent_latency_ms_p99": float(np.percentile(lat, 99)),
+                      "per_waveform_samples_steps_per_s": units / (per_ms / 1e3), "per_waveform_ms": per_ms,
+                      "per_waveform_latency_ms_p50": float(np.percentile(plat, 50)),
+                      "per_waveform_latency_ms_p99": float(np.percentile(plat, 99)),
+                      "host_enqueue_s": time.perf_counter() - t0, "plan": info, "samples_steps": units}))
+    plan.close()
+
+
+def workload_train(args, api):
+    """One LDBP training iteration at 64 x 32768 samples: GPU channel (25 x 80 km, 100 steps/span, ASE),
+    M = 25, T = 31, forward with checkpoints, receiver loss, adjoint, Adam."""
+    import torch
+    from paper_2010_14258_gb300.train import Trainer, TrainConfig
+    cfg = TrainConfig(batch=64, nsym=16384, n_spans=25, channel_steps=100, t_start=31, t_end=3, iters=1000,
+                      lr=1e-3, seed=3)
+    tr = Trainer(cfg)
+    it_ms = time_fn(lambda: tr.train_step(tr.step_count), 5, 2)
+    sd, pw, yw = tr.frames(0)
+    ch_ms = time_fn(lambda: tr.frames(0), 5, 1)
+    fw_ms = time_fn(lambda: api.ldbp_apply(tr.taps, tr.T, tr.c, yw, ckpt=tr.ckpt, out=tr.out), 5, 1)
+    st, _, g = api.rx(tr.out, sd, pw, grad=True)
+    bw_ms = time_fn(lambda: api.ldbp_backward(tr.taps, tr.T, tr.c, tr.ckpt, g, want_gx=False), 5, 1)
+    print(json.dumps({"workload": "train_64x32768_M25_T31", "ms_per_iteration": it_ms, "channel_ms": ch_ms,
+                      "ldbp_forward_ckpt_ms": fw_ms, "ldbp_backward_ms": bw_ms,
+                      "taps_after": int(sum(tr.T))}))
+
+
 def train_model(T: int, iters: int, rank: int):
     """Train LDBP with filter length T on the GPU on short frames of the same link."""
     from paper_2010_14258_gb300.train import Trainer, TrainConfig
@@ -288,6 +410,12 @@ def main():
 
     if args.profile:
         return profile_only(args, api)
+    if args.workload == "channel":
+        return workload_channel(args, api)
+    if args.workload == "ragged":
+        return workload_ragged(args, api)
+    if args.workload == "train":
+        return workload_train(args, api)
 
     fib = synth.Fiber()
     t_setup = time.perf_counter()

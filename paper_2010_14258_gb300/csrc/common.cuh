@@ -131,6 +131,38 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   device_flag(kDevTimeout);
   return false;
 }
+// Wait with acquire semantics at cluster scope (data written by peer blocks
+// through st.async is visible after it returns true).
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster_bounded(uint64_t* bar, uint32_t parity, int limit = 1 << 22) {
+  for (int it = 0; it < limit; ++it)
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+  device_flag(kDevTimeout);
+  return false;
+}
+// Shared-memory address of the same variable in block `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t local_addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+  return r;
+}
+// Asynchronous remote store of one complex value into a peer block's shared
+// memory; the peer's mbarrier `rbar` counts the 8 bytes on arrival.
+__device__ __forceinline__ void st_async_c64(uint32_t raddr, float2 v, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+               "f"(v.x), "f"(v.y), "r"(rbar)
+               : "memory");
+}
+
 // 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
   asm volatile(

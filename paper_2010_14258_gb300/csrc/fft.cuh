@@ -33,21 +33,26 @@ __device__ __forceinline__ float2 tw16(float2 v) {
   }
 }
 
+// Complex add / subtract as one packed FP32x2 instruction each (a - b is
+// fma(b, -1, a), exact).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
 __device__ __forceinline__ void dft2(float2& a, float2& b) {
   const float2 t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
+  a = padd(t, b);
+  b = psub(t, b);
 }
 
 // 4-point DFT on (a0, a1, a2, a3), natural order.
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
-  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
-  const float2 d = csub(a1, a3);
+  const float2 t0 = padd(a0, a2), t1 = psub(a0, a2), t2 = padd(a1, a3);
+  const float2 d = psub(a1, a3);
   const float2 t3 = make_float2(d.y, -d.x);  // -j (a1 - a3)
-  a0 = cadd(t0, t2);
-  a2 = csub(t0, t2);
-  a1 = cadd(t1, t3);
-  a3 = csub(t1, t3);
+  a0 = padd(t0, t2);
+  a2 = psub(t0, t2);
+  a1 = padd(t1, t3);
+  a3 = psub(t1, t3);
 }
 
 template <int R>

@@ -38,8 +38,9 @@ int ssm_choose_cluster(long long n, int batch, int sm_count, int* P, int* log_n2
   while ((1LL << logn) < n) ++logn;
   if ((1LL << logn) != n || logn < kSsmMinLogN2 || logn > kSsmMaxLogN2 + 4) return -1;
   int p = 1;
-  while (logn - __builtin_ctz(p) > kSsmMaxLogN2) p *= 2;
-  if (p > kSsmMaxCluster) return -1;
+  // blocks of at most 4096 samples (two or three blocks per SM) while the cluster allows
+  while (logn - __builtin_ctz(p) > 12 && p < kSsmMaxCluster) p *= 2;
+  if (logn - __builtin_ctz(p) > kSsmMaxLogN2) return -1;
   // more blocks per waveform while the batch alone does not fill the GPU
   while (p < 16 && logn - __builtin_ctz(p) - 1 >= 11 && (long long)batch * p < sm_count) p *= 2;
   *P = p;

@@ -10,11 +10,12 @@
 //   block r holds the decimated sequence x_r[m2] = x[r + P m2];
 //   1. local N2-point Stockham FFT in shared memory (radix 16, conflict-free
 //      padded layout): Y_r[k2];
-//   2. each block takes a chunk of k2 and, for every r, reads Y_r[k2] from the
-//      peer's shared memory (DSMEM), multiplies by exp(-j 2 pi r k2 / n),
-//      runs the P-point DFT over r -> X[k2 + N2 k1], applies the step's
-//      spectral multiply (and noise), conjugates, runs the P-point DFT again,
-//      multiplies by the same twiddles and writes back to block r;
+//   2. every block pushes chunk q of Y_r (a range of k2) into block q's receive
+//      buffer by remote (DSMEM) stores; block q then, for each of its k2,
+//      multiplies Y_r[k2] by exp(-j 2 pi r k2 / n), runs the P-point DFT over
+//      r -> X[k2 + N2 k1], applies the step's spectral multiply (and noise),
+//      conjugates, runs the P-point DFT again, multiplies by the same twiddles
+//      and pushes the value for r back to block r;
 //   3. local N2-point FFT of the conjugated data; conjugating its output gives
 //      the inverse transform, and the Kerr rotation is applied in registers
 //      before the result is stored.
@@ -67,7 +68,7 @@ __device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict_
     const int k = j & (Ns - 1);
     if constexpr (Ns > 1) {
 #pragma unroll
-      for (int q = 1; q < R; ++q) a[i * R + q] = cmul(a[i * R + q], __ldg(&tw[(q - 1) * Ns + k]));
+      for (int q = 1; q < R; ++q) a[i * R + q] = cmul(a[i * R + q], tw[(q - 1) * Ns + k]);
     }
     dft<R>(&a[i * R]);
     if constexpr (LAST_OF_INVERSE) {
@@ -100,15 +101,37 @@ __device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl) {
   else __syncthreads();
 }
 
-// Spectral step across the cluster (see file comment, step 2).
+// Spectral step across the cluster (see file comment, step 2).  Data move
+// by asynchronous remote stores (st.async) that count their bytes on the
+// receiver's mbarrier, so each block waits only for the data it needs: no
+// cluster-wide barrier per step.
+//  * bars[0] completes when this block's receive buffer holds all P chunks;
+//  * bars[1] completes when all N2 results for this block have arrived.
+// The ordering needs no further synchronisation: a block pushes results into
+// block r's chunk q only after receiving that chunk from r (so r has read it),
+// and r pushes its next spectrum only after all results of this step arrived
+// (so every owner has finished reading its receive buffer).
 template <int LOGN2, int P>
-__device__ __forceinline__ void ssm_middle(float2* sbuf, cg::cluster_group& cl, int r, int b, const SsmStep& st,
-                                           const SsmParams& p, bool first) {
+__device__ __forceinline__ bool ssm_middle(float2* sbuf, float2* recv, uint64_t* bars, uint32_t phase, int r, int b,
+                                           const SsmStep& st, const SsmParams& p, bool first) {
   constexpr int N2 = 1 << LOGN2, NT = N2 / kSsmE, C = N2 / P, NK = kSsmE / P;
   const int t = threadIdx.x;
-  float2* rem[P];
+  bool ok = true;
+  if constexpr (P > 1) {
+    if (t == 0) {
+      mbar_arrive_expect_tx(&bars[0], N2 * sizeof(float2));
+      mbar_arrive_expect_tx(&bars[1], N2 * sizeof(float2));
+    }
+    const uint32_t recv_l = smem_u32(recv) + (uint32_t)(r * C) * sizeof(float2), bar0_l = smem_u32(&bars[0]);
 #pragma unroll
-  for (int q = 0; q < P; ++q) rem[q] = cl.map_shared_rank(sbuf, q);
+    for (int q = 0; q < P; ++q) {
+      const uint32_t dst = mapa_shared(recv_l, q), rbar = mapa_shared(bar0_l, q);
+#pragma unroll
+      for (int i = 0; i < NK; ++i)
+        st_async_c64(dst + (uint32_t)(t + i * NT) * sizeof(float2), sbuf[spad(q * C + t + i * NT)], rbar);
+    }
+    ok = mbar_wait_cluster_bounded(&bars[0], phase, 1 << 20);
+  }
   const float2* __restrict__ H = p.tabs[st.tab];
   const float2* __restrict__ HN = st.noise_tab >= 0 ? p.tabs[st.noise_tab] : nullptr;
   const bool noise = st.noise_tab > -2;
@@ -121,10 +144,10 @@ __device__ __forceinline__ void ssm_middle(float2* sbuf, cg::cluster_group& cl, 
   float2 out[NK][P];
 #pragma unroll
   for (int i = 0; i < NK; ++i) {
-    const int k2 = r * C + t + i * NT;
+    const int kk = t + i * NT, k2 = r * C + kk;
     float2 a[P], w[P];
 #pragma unroll
-    for (int q = 0; q < P; ++q) a[q] = rem[q][spad(k2)];
+    for (int q = 0; q < P; ++q) a[q] = P > 1 ? recv[q * C + kk] : sbuf[spad(k2)];
     w[0] = make_float2(1.f, 0.f);
 #pragma unroll
     for (int q = 1; q < P; ++q) {
@@ -148,20 +171,33 @@ __device__ __forceinline__ void ssm_middle(float2* sbuf, cg::cluster_group& cl, 
 #pragma unroll
     for (int q = 0; q < P; ++q) out[i][q] = cmul(a[q], w[q]);
   }
-  cluster_barrier<P>(cl);  // every read of the peers' spectra has completed
+  if constexpr (P > 1) {
+    const uint32_t bar1_l = smem_u32(&bars[1]);
 #pragma unroll
-  for (int i = 0; i < NK; ++i) {
-    const int k2 = r * C + t + i * NT;
+    for (int q = 0; q < P; ++q) {
+      const uint32_t dst = mapa_shared(smem_u32(sbuf), q), rbar = mapa_shared(bar1_l, q);
 #pragma unroll
-    for (int q = 0; q < P; ++q) rem[q][spad(k2)] = out[i][q];
+      for (int i = 0; i < NK; ++i)
+        st_async_c64(dst + (uint32_t)spad(r * C + t + i * NT) * sizeof(float2), out[i][q], rbar);
+    }
+    ok = mbar_wait_cluster_bounded(&bars[1], phase, 1 << 20) && ok;
+  } else {
+#pragma unroll
+    for (int i = 0; i < NK; ++i) sbuf[spad(t + i * NT)] = out[i][0];
+    __syncthreads();
   }
-  cluster_barrier<P>(cl);  // every write has landed before the local transforms
+  return ok;
 }
 
 template <int LOGN2, int P>
 __global__ void __launch_bounds__((1 << LOGN2) / kSsmE, (512 / ((1 << LOGN2) / kSsmE)) > 1 ? (512 / ((1 << LOGN2) / kSsmE)) : 1) ssm_kernel(const __grid_constant__ SsmParams p) {
   constexpr int N2 = 1 << LOGN2, NT = N2 / kSsmE;
-  extern __shared__ __align__(16) float2 sbuf[];
+  extern __shared__ __align__(16) float2 sbuf[];  // [spad(N2)] data, then the local-pass twiddles
+  constexpr int NTW = ssm_stage_offset(LOGN2, LOGN2);
+  float2* stw = sbuf + N2 + N2 / 16;
+  float2* recv = stw + NTW;  // [P][N2/P] receive buffer of the cluster exchange (P > 1)
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ int stop;
   cg::cluster_group cl = cg::this_cluster();
   const int r = (int)cl.block_rank();
   const int b = blockIdx.x / P;
@@ -173,15 +209,22 @@ __global__ void __launch_bounds__((1 << LOGN2) / kSsmE, (512 / ((1 << LOGN2) / k
     if (p.c_pre != 0.f) v = kerr_rotate_precise<true>(v, p.c_pre);
     sbuf[spad(m2)] = v;
   }
-  __syncthreads();
-  const float2* stw = p.twiddle + (P - 1) * N2;
+  for (int i = t; i < NTW; i += NT) stw[i] = p.twiddle[(P - 1) * N2 + i];
+  if (t == 0) {
+    stop = 0;
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  cluster_barrier<P>(cl);  // every block of the cluster is running (barriers initialised) before remote access
   for (int s = 0; s < p.nsteps; ++s) {
     const SsmStep st = p.steps[s];
     ssm_local_fft<LOGN2, 0, false>(sbuf, stw, 0.f);
-    cluster_barrier<P>(cl);  // all spectra of the cluster are ready
-    ssm_middle<LOGN2, P>(sbuf, cl, r, b, st, p, s == 0);
-    ssm_local_fft<LOGN2, 0, true>(sbuf, stw, st.c);
+    if (!ssm_middle<LOGN2, P>(sbuf, recv, bars, (uint32_t)(s & 1), r, b, st, p, s == 0)) stop = 1;
+    ssm_local_fft<LOGN2, 0, true>(sbuf, stw, st.c);  // its barriers make `stop` visible
+    if (stop) break;
   }
+  cluster_barrier<P>(cl);  // no block leaves while a peer may still store into it
   float2* __restrict__ yout = p.y + (long long)b * n;
   for (int m2 = t; m2 < N2; m2 += NT) yout[r + (long long)P * m2] = sbuf[spad(m2)];
 }
@@ -189,7 +232,7 @@ __global__ void __launch_bounds__((1 << LOGN2) / kSsmE, (512 / ((1 << LOGN2) / k
 template <int LOGN2, int P>
 cudaError_t launch_one(const SsmParams& p, cudaStream_t st) {
   constexpr int N2 = 1 << LOGN2, NT = N2 / kSsmE;
-  const size_t smem = sizeof(float2) * (size_t)(N2 + N2 / 16);
+  const size_t smem = sizeof(float2) * (size_t)(N2 + N2 / 16 + ssm_stage_offset(LOGN2, LOGN2) + (P > 1 ? N2 : 0));
   auto kern = ssm_kernel<LOGN2, P>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
