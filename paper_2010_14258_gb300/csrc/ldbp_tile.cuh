@@ -77,64 +77,81 @@ __device__ __forceinline__ void tile_fir(const float2 (&xe)[kFwdR + 2 * K], cons
   }
 }
 
-// exp(j phi) for two phases at once (packed FP32x2), |phi| <= pi/4: the
-// Taylor polynomials of expj<false> evaluated on (phi_a, phi_b).
-__device__ __forceinline__ void expj_pair(float2 phi, float2& c, float2& s) {
-  const float2 r2 = __fmul2_rn(phi, phi);
-  float2 ps = __ffma2_rn(r2, make_float2(2.75573192239858907e-6f, 2.75573192239858907e-6f),
-                         make_float2(-1.98412698412698413e-4f, -1.98412698412698413e-4f));
-  ps = __ffma2_rn(r2, ps, make_float2(8.33333333333333333e-3f, 8.33333333333333333e-3f));
-  ps = __ffma2_rn(r2, ps, make_float2(-1.66666666666666667e-1f, -1.66666666666666667e-1f));
-  s = __ffma2_rn(__fmul2_rn(r2, phi), ps, phi);
-  float2 pc = __ffma2_rn(r2, make_float2(-2.75573192239858907e-7f, -2.75573192239858907e-7f),
-                         make_float2(2.48015873015873016e-5f, 2.48015873015873016e-5f));
-  pc = __ffma2_rn(r2, pc, make_float2(-1.38888888888888889e-3f, -1.38888888888888889e-3f));
-  pc = __ffma2_rn(r2, pc, make_float2(4.16666666666666667e-2f, 4.16666666666666667e-2f));
-  pc = __ffma2_rn(r2, pc, make_float2(-0.5f, -0.5f));
-  c = __ffma2_rn(r2, pc, make_float2(1.0f, 1.0f));
+// Taylor coefficients of sin(c p) and cos(c p) as polynomials in the power
+// p = |v|^2 (c folded in): sin = p (s1 + p^2 (s3 + p^2 (s5 + ...))),
+// cos = 1 + p^2 (c2 + p^2 (c4 + ...)).  Computed once per step.
+struct KerrPoly {
+  float s1, s3, s5, s7, s9, c2, c4, c6, c8, c10;
+};
+
+__device__ __forceinline__ KerrPoly kerr_poly(float c) {
+  KerrPoly k;
+  const float c2 = c * c;
+  k.s1 = c;
+  k.s3 = k.s1 * c2 * -1.66666666666666667e-1f;  // / (2 * 3)
+  k.s5 = k.s3 * c2 * -5.0e-2f;                  // / (4 * 5)
+  k.s7 = k.s5 * c2 * -2.38095238095238095e-2f;  // / (6 * 7)
+  k.s9 = k.s7 * c2 * -1.38888888888888889e-2f;  // / (8 * 9)
+  k.c2 = c2 * -0.5f;
+  k.c4 = k.c2 * c2 * -8.33333333333333333e-2f;  // / (3 * 4)
+  k.c6 = k.c4 * c2 * -3.33333333333333333e-2f;  // / (5 * 6)
+  k.c8 = k.c6 * c2 * -1.78571428571428571e-2f;  // / (7 * 8)
+  k.c10 = k.c8 * c2 * -1.11111111111111111e-2f; // / (9 * 10)
+  return k;
 }
 
-// The same for |phi| <= 1/4, where the Taylor series truncated after phi^5
-// (sine) and phi^6 (cosine) is below 1.2e-8 and 3.8e-10, under half an FP32
-// ulp of the unit-modulus result.
-__device__ __forceinline__ void expj_pair_small(float2 phi, float2& c, float2& s) {
-  const float2 r2 = __fmul2_rn(phi, phi);
-  const float2 ps = __ffma2_rn(r2, make_float2(8.33333333333333333e-3f, 8.33333333333333333e-3f),
-                               make_float2(-1.66666666666666667e-1f, -1.66666666666666667e-1f));
-  s = __ffma2_rn(__fmul2_rn(r2, phi), ps, phi);
-  float2 pc = __ffma2_rn(r2, make_float2(-1.38888888888888889e-3f, -1.38888888888888889e-3f),
-                         make_float2(4.16666666666666667e-2f, 4.16666666666666667e-2f));
-  pc = __ffma2_rn(r2, pc, make_float2(-0.5f, -0.5f));
-  c = __ffma2_rn(r2, pc, make_float2(1.0f, 1.0f));
-}
-
-// Phases phi[r] = c |v[r]|^2 of the thread's samples and their maximum magnitude.
-__device__ __forceinline__ float tile_phases(const float2 (&v)[kFwdR], float c, float (&phi)[kFwdR]) {
+// Powers p[r] = |v[r]|^2 of the thread's samples and their maximum.
+__device__ __forceinline__ float tile_power(const float2 (&v)[kFwdR], float (&p)[kFwdR]) {
   float m = 0.f;
 #pragma unroll
-  for (int r = 0; r < kFwdR; r += 2) {
-    const float2 a = __fmul2_rn(v[r], v[r]), b = __fmul2_rn(v[r + 1], v[r + 1]);
-    const float2 p = __fmul2_rn(make_float2(a.x + a.y, b.x + b.y), make_float2(c, c));
-    phi[r] = p.x;
-    phi[r + 1] = p.y;
-    m = fmaxf(m, fmaxf(fabsf(p.x), fabsf(p.y)));
+  for (int r = 0; r < kFwdR; ++r) {
+    p[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+    m = fmaxf(m, p[r]);
   }
   return m;
 }
 
+// (cos, sin)(c p) for two powers at once, |c p| <= 1/4: series truncated after
+// (c p)^5 / (c p)^6 (error below 1.2e-8 / 3.8e-10, under half an FP32 ulp).
+__device__ __forceinline__ void kerr_pair_small(float2 P, const KerrPoly& k, float2& cs, float2& sn) {
+  const float2 r2 = __fmul2_rn(P, P);
+  float2 t = __ffma2_rn(r2, make_float2(k.s5, k.s5), make_float2(k.s3, k.s3));
+  t = __ffma2_rn(r2, t, make_float2(k.s1, k.s1));
+  sn = __fmul2_rn(P, t);
+  float2 u = __ffma2_rn(r2, make_float2(k.c6, k.c6), make_float2(k.c4, k.c4));
+  u = __ffma2_rn(r2, u, make_float2(k.c2, k.c2));
+  cs = __ffma2_rn(r2, u, make_float2(1.f, 1.f));
+}
+
+// The same for |c p| <= pi/4 (series to (c p)^9 / (c p)^10, error below 2e-9).
+__device__ __forceinline__ void kerr_pair(float2 P, const KerrPoly& k, float2& cs, float2& sn) {
+  const float2 r2 = __fmul2_rn(P, P);
+  float2 t = __ffma2_rn(r2, make_float2(k.s9, k.s9), make_float2(k.s7, k.s7));
+  t = __ffma2_rn(r2, t, make_float2(k.s5, k.s5));
+  t = __ffma2_rn(r2, t, make_float2(k.s3, k.s3));
+  t = __ffma2_rn(r2, t, make_float2(k.s1, k.s1));
+  sn = __fmul2_rn(P, t);
+  float2 u = __ffma2_rn(r2, make_float2(k.c10, k.c10), make_float2(k.c8, k.c8));
+  u = __ffma2_rn(r2, u, make_float2(k.c6, k.c6));
+  u = __ffma2_rn(r2, u, make_float2(k.c4, k.c4));
+  u = __ffma2_rn(r2, u, make_float2(k.c2, k.c2));
+  cs = __ffma2_rn(r2, u, make_float2(1.f, 1.f));
+}
+
 // e[r] = exp(j c |v[r]|^2).  The polynomial is chosen per warp from the
-// largest phase: |phi| <= 1/4 (the usual case: the nonlinear phase per step
-// is small) and |phi| <= pi/4 use packed FP32x2 Taylor polynomials without
-// range reduction; larger phases take the reducing scalar path.  Every path
-// is accurate to about one FP32 ulp.
+// largest phase: |c p| <= 1/4 (the usual case: the nonlinear phase per step
+// is small) and <= pi/4 use packed FP32x2 Taylor series in p; larger phases
+// take the range-reducing scalar path (expj).  Every path is accurate to
+// about one FP32 ulp.
 __device__ __forceinline__ void tile_expj(const float2 (&v)[kFwdR], float c, float2 (&e)[kFwdR]) {
-  float phi[kFwdR];
-  const float m = tile_phases(v, c, phi);
+  float p[kFwdR];
+  const float m = tile_power(v, p) * fabsf(c);
+  const KerrPoly k = kerr_poly(c);
   if (__all_sync(0xffffffffu, m <= 0.25f)) {
 #pragma unroll
     for (int r = 0; r < kFwdR; r += 2) {
       float2 cc, ss;
-      expj_pair_small(make_float2(phi[r], phi[r + 1]), cc, ss);
+      kerr_pair_small(make_float2(p[r], p[r + 1]), k, cc, ss);
       e[r] = make_float2(cc.x, ss.x);
       e[r + 1] = make_float2(cc.y, ss.y);
     }
@@ -142,26 +159,27 @@ __device__ __forceinline__ void tile_expj(const float2 (&v)[kFwdR], float c, flo
 #pragma unroll
     for (int r = 0; r < kFwdR; r += 2) {
       float2 cc, ss;
-      expj_pair(make_float2(phi[r], phi[r + 1]), cc, ss);
+      kerr_pair(make_float2(p[r], p[r + 1]), k, cc, ss);
       e[r] = make_float2(cc.x, ss.x);
       e[r + 1] = make_float2(cc.y, ss.y);
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < kFwdR; ++r) e[r] = expj<true>(phi[r]);
+    for (int r = 0; r < kFwdR; ++r) e[r] = expj<true>(c * p[r]);
   }
 }
 
 // v[r] <- v[r] exp(j c |v[r]|^2) in place (the Kerr step), without
 // materialising the rotation pairs.
 __device__ __forceinline__ void tile_kerr(float2 (&v)[kFwdR], float c) {
-  float phi[kFwdR];
-  const float m = tile_phases(v, c, phi);
+  float p[kFwdR];
+  const float m = tile_power(v, p) * fabsf(c);
+  const KerrPoly k = kerr_poly(c);
   if (__all_sync(0xffffffffu, m <= 0.25f)) {
 #pragma unroll
     for (int r = 0; r < kFwdR; r += 2) {
       float2 cc, ss;
-      expj_pair_small(make_float2(phi[r], phi[r + 1]), cc, ss);
+      kerr_pair_small(make_float2(p[r], p[r + 1]), k, cc, ss);
       v[r] = make_float2(fmaf(v[r].x, cc.x, -v[r].y * ss.x), fmaf(v[r].x, ss.x, v[r].y * cc.x));
       v[r + 1] = make_float2(fmaf(v[r + 1].x, cc.y, -v[r + 1].y * ss.y), fmaf(v[r + 1].x, ss.y, v[r + 1].y * cc.y));
     }
@@ -169,13 +187,13 @@ __device__ __forceinline__ void tile_kerr(float2 (&v)[kFwdR], float c) {
 #pragma unroll
     for (int r = 0; r < kFwdR; r += 2) {
       float2 cc, ss;
-      expj_pair(make_float2(phi[r], phi[r + 1]), cc, ss);
+      kerr_pair(make_float2(p[r], p[r + 1]), k, cc, ss);
       v[r] = make_float2(fmaf(v[r].x, cc.x, -v[r].y * ss.x), fmaf(v[r].x, ss.x, v[r].y * cc.x));
       v[r + 1] = make_float2(fmaf(v[r + 1].x, cc.y, -v[r + 1].y * ss.y), fmaf(v[r + 1].x, ss.y, v[r + 1].y * cc.y));
     }
   } else {
 #pragma unroll
-    for (int r = 0; r < kFwdR; ++r) v[r] = cmul(v[r], expj<true>(phi[r]));
+    for (int r = 0; r < kFwdR; ++r) v[r] = cmul(v[r], expj<true>(c * p[r]));
   }
 }
 
