@@ -32,10 +32,10 @@ int cuda_fail(cudaError_t e, const char* what) {
   return fail(LDBP_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-int make_tile_plan(long long n, int H, TilePlan* out) {
+int make_tile_plan(long long n, int H, TilePlan* out, int S) {
   const int Hp = H + (H & 1);
-  if (2 * Hp > kFwdS / 2) return -1;
-  const int Lmax = kFwdS - 2 * Hp;
+  if (2 * Hp > S / 2) return -1;
+  const int Lmax = S - 2 * Hp;
   if (Lmax < 2) return -1;
   long long tpw = (n + Lmax - 1) / Lmax;
   long long L = (n + tpw - 1) / tpw;
@@ -107,8 +107,11 @@ int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const fl
   if (overlaps(x, bytes, y, bytes)) return fail(LDBP_EINVAL, "x and y overlap");
   if (ckpt && (overlaps(ckpt, bytes * M, x, bytes) || overlaps(ckpt, bytes * M, y, bytes)))
     return fail(LDBP_EINVAL, "ckpt overlaps x or y");
+  int Ks[LDBP_MAX_STEPS];
+  for (int i = 0; i < M; ++i) Ks[i] = (T[i] - 1) / 2;
   TilePlan plan;
-  if (make_tile_plan(n, H, &plan)) return fail(LDBP_EINVAL, "halo sum %d too large for one tile", H);
+  if (make_tile_plan(n, H, &plan, fwd_tile_samples(Ks, M, kmax)))
+    return fail(LDBP_EINVAL, "halo sum %d too large for one tile", H);
   if ((long long)plan.tiles_per_wave * batch > 0x7fffffffLL) return fail(LDBP_EINVAL, "grid too large");
   FwdParams p;
   memset(&p, 0, sizeof(p));

@@ -34,10 +34,12 @@ struct FwdParams {
 struct TilePlan {
   int Hp, L, tiles_per_wave;
 };
-int make_tile_plan(long long n, int H, TilePlan* out);
+int make_tile_plan(long long n, int H, TilePlan* out, int S = kFwdS);
 
 cudaError_t launch_ldbp_fwd(const FwdParams& p, int kmax_needed, cudaStream_t st);
-size_t fwd_smem_bytes(int kmax, int M);
+size_t fwd_smem_bytes(int kmax, int M, int S);
+// Tile size (samples) of the forward instance chosen for these step widths.
+int fwd_tile_samples(const int* K, int M, int kmax_needed);
 int fwd_kmax_class(int kmax_needed);
 
 }  // namespace ldbp

@@ -11,8 +11,8 @@ namespace ldbp {
 // xe[0..K) = the K samples left of v, xe[K..K+R) = v, xe[K+R..K+R+K) = the K
 // samples right of v.  The first (last) warp of the block sees zeros beyond
 // the tile.  Contains one __syncthreads (edge exchange between warps).
-template <int K>
-__device__ __forceinline__ void tile_extend(const float2 (&v)[kFwdR], float2 (&xe)[kFwdR + 2 * K], float2* edge_first,
+template <int K, int R = kFwdR, int NW = kFwdNW>
+__device__ __forceinline__ void tile_extend(const float2 (&v)[R], float2 (&xe)[R + 2 * K], float2* edge_first,
                                             float2* edge_last, int lane, int warp) {
   if constexpr (K > 0) {
     if (lane == 0) {
@@ -21,15 +21,15 @@ __device__ __forceinline__ void tile_extend(const float2 (&v)[kFwdR], float2 (&x
     }
     if (lane == 31) {
 #pragma unroll
-      for (int j = 0; j < K; ++j) edge_last[warp * kFwdEdge + j] = v[kFwdR - K + j];
+      for (int j = 0; j < K; ++j) edge_last[warp * kFwdEdge + j] = v[R - K + j];
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      xe[j].x = __shfl_up_sync(0xffffffffu, v[kFwdR - K + j].x, 1);
-      xe[j].y = __shfl_up_sync(0xffffffffu, v[kFwdR - K + j].y, 1);
-      xe[K + kFwdR + j].x = __shfl_down_sync(0xffffffffu, v[j].x, 1);
-      xe[K + kFwdR + j].y = __shfl_down_sync(0xffffffffu, v[j].y, 1);
+      xe[j].x = __shfl_up_sync(0xffffffffu, v[R - K + j].x, 1);
+      xe[j].y = __shfl_up_sync(0xffffffffu, v[R - K + j].y, 1);
+      xe[K + R + j].x = __shfl_down_sync(0xffffffffu, v[j].x, 1);
+      xe[K + R + j].y = __shfl_down_sync(0xffffffffu, v[j].y, 1);
     }
     if (lane == 0) {
 #pragma unroll
@@ -39,11 +39,11 @@ __device__ __forceinline__ void tile_extend(const float2 (&v)[kFwdR], float2 (&x
     if (lane == 31) {
 #pragma unroll
       for (int j = 0; j < K; ++j)
-        xe[K + kFwdR + j] = warp < kFwdNW - 1 ? edge_first[(warp + 1) * kFwdEdge + j] : make_float2(0.f, 0.f);
+        xe[K + R + j] = warp < NW - 1 ? edge_first[(warp + 1) * kFwdEdge + j] : make_float2(0.f, 0.f);
     }
   }
 #pragma unroll
-  for (int r = 0; r < kFwdR; ++r) xe[K + r] = v[r];
+  for (int r = 0; r < R; ++r) xe[K + r] = v[r];
 }
 
 // Taps pre-expanded for packed FP32x2 arithmetic: (h.re, h.re, h.im, h.im).
@@ -53,9 +53,9 @@ __device__ __forceinline__ float4 tap_pair(float2 h) { return make_float4(h.x, h
 // with CONJ the taps are conjugated (the adjoint filter).  Packed FP32x2
 // form: A accumulates h.re * (s.re, s.im) and Bv accumulates h.im * (s.re, s.im),
 // so h s = (A.re - Bv.im, A.im + Bv.re): 3 packed instructions per tap pair.
-template <int K, bool CONJ>
-__device__ __forceinline__ void tile_fir(const float2 (&xe)[kFwdR + 2 * K], const float4* __restrict__ h4,
-                                         float2 (&out)[kFwdR]) {
+template <int K, bool CONJ, int R = kFwdR>
+__device__ __forceinline__ void tile_fir(const float2 (&xe)[R + 2 * K], const float4* __restrict__ h4,
+                                         float2 (&out)[R]) {
   float2 hr[K + 1], hi[K + 1];
 #pragma unroll
   for (int k = 0; k <= K; ++k) {
@@ -64,7 +64,7 @@ __device__ __forceinline__ void tile_fir(const float2 (&xe)[kFwdR + 2 * K], cons
     hi[k] = make_float2(q.z, q.w);
   }
 #pragma unroll
-  for (int r = 0; r < kFwdR; ++r) {
+  for (int r = 0; r < R; ++r) {
     float2 A = __fmul2_rn(hr[0], xe[K + r]);
     float2 Bv = __fmul2_rn(hi[0], xe[K + r]);
 #pragma unroll
@@ -101,24 +101,38 @@ __device__ __forceinline__ KerrPoly kerr_poly(float c) {
 }
 
 // Powers p[r] = |v[r]|^2 of the thread's samples and their maximum.
-__device__ __forceinline__ float tile_power(const float2 (&v)[kFwdR], float (&p)[kFwdR]) {
+template <int R = kFwdR>
+__device__ __forceinline__ float tile_power(const float2 (&v)[R], float (&p)[R]) {
   float m = 0.f;
 #pragma unroll
-  for (int r = 0; r < kFwdR; ++r) {
+  for (int r = 0; r < R; ++r) {
     p[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
     m = fmaxf(m, p[r]);
   }
   return m;
 }
 
-// (cos, sin)(c p) for two powers at once, |c p| <= 1/4: series truncated after
-// (c p)^5 / (c p)^6 (error below 1.2e-8 / 3.8e-10, under half an FP32 ulp).
+// (cos, sin)(c p) for two powers at once, |c p| <= 0.3: series truncated after
+// (c p)^5 / (c p)^6 (truncation below 4.4e-8 / 1.7e-9, under half an FP32 ulp of 1).
 __device__ __forceinline__ void kerr_pair_small(float2 P, const KerrPoly& k, float2& cs, float2& sn) {
   const float2 r2 = __fmul2_rn(P, P);
   float2 t = __ffma2_rn(r2, make_float2(k.s5, k.s5), make_float2(k.s3, k.s3));
   t = __ffma2_rn(r2, t, make_float2(k.s1, k.s1));
   sn = __fmul2_rn(P, t);
   float2 u = __ffma2_rn(r2, make_float2(k.c6, k.c6), make_float2(k.c4, k.c4));
+  u = __ffma2_rn(r2, u, make_float2(k.c2, k.c2));
+  cs = __ffma2_rn(r2, u, make_float2(1.f, 1.f));
+}
+
+// |c p| <= 0.6: series to (c p)^7 / (c p)^8 (truncation below 2.9e-8 / 1.8e-9).
+__device__ __forceinline__ void kerr_pair_mid(float2 P, const KerrPoly& k, float2& cs, float2& sn) {
+  const float2 r2 = __fmul2_rn(P, P);
+  float2 t = __ffma2_rn(r2, make_float2(k.s7, k.s7), make_float2(k.s5, k.s5));
+  t = __ffma2_rn(r2, t, make_float2(k.s3, k.s3));
+  t = __ffma2_rn(r2, t, make_float2(k.s1, k.s1));
+  sn = __fmul2_rn(P, t);
+  float2 u = __ffma2_rn(r2, make_float2(k.c8, k.c8), make_float2(k.c6, k.c6));
+  u = __ffma2_rn(r2, u, make_float2(k.c4, k.c4));
   u = __ffma2_rn(r2, u, make_float2(k.c2, k.c2));
   cs = __ffma2_rn(r2, u, make_float2(1.f, 1.f));
 }
@@ -138,63 +152,63 @@ __device__ __forceinline__ void kerr_pair(float2 P, const KerrPoly& k, float2& c
   cs = __ffma2_rn(r2, u, make_float2(1.f, 1.f));
 }
 
-// e[r] = exp(j c |v[r]|^2).  The polynomial is chosen per warp from the
-// largest phase: |c p| <= 1/4 (the usual case: the nonlinear phase per step
-// is small) and <= pi/4 use packed FP32x2 Taylor series in p; larger phases
-// take the range-reducing scalar path (expj).  Every path is accurate to
-// about one FP32 ulp.
-__device__ __forceinline__ void tile_expj(const float2 (&v)[kFwdR], float c, float2 (&e)[kFwdR]) {
-  float p[kFwdR];
+// Phase tiers of the Kerr step, chosen per warp from its largest phase
+// |c p|: the usual per-step nonlinear phase is well below 0.3.
+constexpr float kKerrTierA = 0.3f, kKerrTierB = 0.6f, kKerrTierC = 0.785398163f;
+
+// e[r] = exp(j c |v[r]|^2).  Packed FP32x2 Taylor series in p for
+// |c p| <= 0.3, 0.6 and pi/4 (tiers A, B, C), the range-reducing scalar path
+// (expj) beyond; every path is accurate to about one FP32 ulp.
+template <int R = kFwdR>
+__device__ __forceinline__ void tile_expj(const float2 (&v)[R], float c, float2 (&e)[R]) {
+  float p[R];
   const float m = tile_power(v, p) * fabsf(c);
   const KerrPoly k = kerr_poly(c);
-  if (__all_sync(0xffffffffu, m <= 0.25f)) {
-#pragma unroll
-    for (int r = 0; r < kFwdR; r += 2) {
-      float2 cc, ss;
-      kerr_pair_small(make_float2(p[r], p[r + 1]), k, cc, ss);
-      e[r] = make_float2(cc.x, ss.x);
-      e[r + 1] = make_float2(cc.y, ss.y);
-    }
-  } else if (__all_sync(0xffffffffu, m <= 0.785398163f)) {
-#pragma unroll
-    for (int r = 0; r < kFwdR; r += 2) {
-      float2 cc, ss;
-      kerr_pair(make_float2(p[r], p[r + 1]), k, cc, ss);
-      e[r] = make_float2(cc.x, ss.x);
-      e[r + 1] = make_float2(cc.y, ss.y);
-    }
+#define LDBP_EXPJ_TIER(fn)                                 \
+  _Pragma("unroll") for (int r = 0; r < R; r += 2) {   \
+    float2 cc, ss;                                         \
+    fn(make_float2(p[r], p[r + 1]), k, cc, ss);            \
+    e[r] = make_float2(cc.x, ss.x);                        \
+    e[r + 1] = make_float2(cc.y, ss.y);                    \
+  }
+  if (__all_sync(0xffffffffu, m <= kKerrTierA)) {
+    LDBP_EXPJ_TIER(kerr_pair_small)
+  } else if (__all_sync(0xffffffffu, m <= kKerrTierB)) {
+    LDBP_EXPJ_TIER(kerr_pair_mid)
+  } else if (__all_sync(0xffffffffu, m <= kKerrTierC)) {
+    LDBP_EXPJ_TIER(kerr_pair)
   } else {
 #pragma unroll
-    for (int r = 0; r < kFwdR; ++r) e[r] = expj<true>(c * p[r]);
+    for (int r = 0; r < R; ++r) e[r] = expj<true>(c * p[r]);
   }
+#undef LDBP_EXPJ_TIER
 }
 
 // v[r] <- v[r] exp(j c |v[r]|^2) in place (the Kerr step), without
-// materialising the rotation pairs.
-__device__ __forceinline__ void tile_kerr(float2 (&v)[kFwdR], float c) {
-  float p[kFwdR];
+// materialising the rotation pairs; same tiers as tile_expj.
+template <int R = kFwdR>
+__device__ __forceinline__ void tile_kerr(float2 (&v)[R], float c) {
+  float p[R];
   const float m = tile_power(v, p) * fabsf(c);
   const KerrPoly k = kerr_poly(c);
-  if (__all_sync(0xffffffffu, m <= 0.25f)) {
-#pragma unroll
-    for (int r = 0; r < kFwdR; r += 2) {
-      float2 cc, ss;
-      kerr_pair_small(make_float2(p[r], p[r + 1]), k, cc, ss);
-      v[r] = make_float2(fmaf(v[r].x, cc.x, -v[r].y * ss.x), fmaf(v[r].x, ss.x, v[r].y * cc.x));
-      v[r + 1] = make_float2(fmaf(v[r + 1].x, cc.y, -v[r + 1].y * ss.y), fmaf(v[r + 1].x, ss.y, v[r + 1].y * cc.y));
-    }
-  } else if (__all_sync(0xffffffffu, m <= 0.785398163f)) {
-#pragma unroll
-    for (int r = 0; r < kFwdR; r += 2) {
-      float2 cc, ss;
-      kerr_pair(make_float2(p[r], p[r + 1]), k, cc, ss);
-      v[r] = make_float2(fmaf(v[r].x, cc.x, -v[r].y * ss.x), fmaf(v[r].x, ss.x, v[r].y * cc.x));
-      v[r + 1] = make_float2(fmaf(v[r + 1].x, cc.y, -v[r + 1].y * ss.y), fmaf(v[r + 1].x, ss.y, v[r + 1].y * cc.y));
-    }
+#define LDBP_KERR_TIER(fn)                                                                                  \
+  _Pragma("unroll") for (int r = 0; r < R; r += 2) {                                                    \
+    float2 cc, ss;                                                                                          \
+    fn(make_float2(p[r], p[r + 1]), k, cc, ss);                                                             \
+    v[r] = make_float2(fmaf(v[r].x, cc.x, -v[r].y * ss.x), fmaf(v[r].x, ss.x, v[r].y * cc.x));              \
+    v[r + 1] = make_float2(fmaf(v[r + 1].x, cc.y, -v[r + 1].y * ss.y), fmaf(v[r + 1].x, ss.y, v[r + 1].y * cc.y)); \
+  }
+  if (__all_sync(0xffffffffu, m <= kKerrTierA)) {
+    LDBP_KERR_TIER(kerr_pair_small)
+  } else if (__all_sync(0xffffffffu, m <= kKerrTierB)) {
+    LDBP_KERR_TIER(kerr_pair_mid)
+  } else if (__all_sync(0xffffffffu, m <= kKerrTierC)) {
+    LDBP_KERR_TIER(kerr_pair)
   } else {
 #pragma unroll
-    for (int r = 0; r < kFwdR; ++r) v[r] = cmul(v[r], expj<true>(c * p[r]));
+    for (int r = 0; r < R; ++r) v[r] = cmul(v[r], expj<true>(c * p[r]));
   }
+#undef LDBP_KERR_TIER
 }
 
 }  // namespace ldbp
