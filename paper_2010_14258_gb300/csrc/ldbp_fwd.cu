@@ -187,8 +187,9 @@ static cudaError_t launch_cls(const FwdParams& p, int grid, cudaStream_t st) {
 }
 
 // Kernel instance for a model.  Uniform filter widths of the usual models
-// (T = 3, 5, 7, 9, 15) get fixed-width instances with 32 samples per thread;
-// mixed widths the per-step dispatch.
+// (T = 3, 5, 7, 9, 15) get fixed-width instances, mixed widths the per-step
+// dispatch.  32 samples per thread in 128-thread blocks except where the
+// per-step dispatch over K <= 2 (or up to 16) runs faster with 16 per thread.
 enum FwdInstance { kFix1, kFix2, kFix3, kFix4, kFix7, kGen2, kGen4, kGen8, kGen16 };
 
 static FwdInstance fwd_select(const int* K, int M, int kmax_needed) {
@@ -214,8 +215,8 @@ static FwdInstance fwd_select(const int* K, int M, int kmax_needed) {
 
 int fwd_tile_samples(const int* K, int M, int kmax_needed) {
   switch (fwd_select(K, M, kmax_needed)) {
-    case kFix1: case kFix2: case kFix3: case kFix4: case kFix7: return 32 * 128;
-    default: return kFwdS;
+    case kGen2: case kGen16: return kFwdR * kFwdNT;
+    default: return 32 * 128;
   }
 }
 
@@ -228,8 +229,8 @@ cudaError_t launch_ldbp_fwd(const FwdParams& p, int kmax_needed, cudaStream_t st
     case kFix4: return launch_cls<4, 4, 4, 32, 128>(p, grid, st);
     case kFix7: return launch_cls<8, 3, 7, 32, 128>(p, grid, st);
     case kGen2: return launch_cls<2, 3, -1>(p, grid, st);
-    case kGen4: return launch_cls<4, 2, -1>(p, grid, st);
-    case kGen8: return launch_cls<8, 2, -1>(p, grid, st);
+    case kGen4: return launch_cls<4, 4, -1, 32, 128>(p, grid, st);
+    case kGen8: return launch_cls<8, 3, -1, 32, 128>(p, grid, st);
     default: return launch_cls<16, 1, -1>(p, grid, st);
   }
 }
