@@ -117,6 +117,19 @@ __device__ __forceinline__ bool ssm_middle(float2* sbuf, float2* recv, uint64_t*
   constexpr int N2 = 1 << LOGN2, NT = N2 / kSsmE, C = N2 / P, NK = kSsmE / P;
   const int t = threadIdx.x;
   bool ok = true;
+  // The step's spectral values and the cluster twiddles of this thread's
+  // frequencies are fetched from global memory first, so that their latency
+  // overlaps the exchange below.
+  const float2* __restrict__ H = p.tabs[st.tab];
+  float2 hv[NK][P], wv[NK][P > 1 ? P - 1 : 1];
+#pragma unroll
+  for (int i = 0; i < NK; ++i) {
+    const int k2 = r * C + t + i * NT;
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) hv[i][k1] = __ldg(&H[k2 + N2 * k1]);
+#pragma unroll
+    for (int q = 1; q < P; ++q) wv[i][q - 1] = __ldg(&p.twiddle[(q - 1) * N2 + k2]);
+  }
   if constexpr (P > 1) {
     if (t == 0) {
       mbar_arrive_expect_tx(&bars[0], N2 * sizeof(float2));
@@ -132,7 +145,6 @@ __device__ __forceinline__ bool ssm_middle(float2* sbuf, float2* recv, uint64_t*
     }
     ok = mbar_wait_cluster_bounded(&bars[0], phase, 1 << 20);
   }
-  const float2* __restrict__ H = p.tabs[st.tab];
   const float2* __restrict__ HN = st.noise_tab >= 0 ? p.tabs[st.noise_tab] : nullptr;
   const bool noise = st.noise_tab > -2;
   const float flat = 1.0f / (float)p.n;
@@ -141,24 +153,20 @@ __device__ __forceinline__ bool ssm_middle(float2* sbuf, float2* recv, uint64_t*
     const float w = p.wave_scale[b];
     sc *= p.wave_mode == 1 ? sqrtf(w) : p.wave_mode == 2 ? rsqrtf(w) : w;
   }
-  float2 out[NK][P];
+  const uint32_t bar1_l = smem_u32(&bars[1]);
 #pragma unroll
   for (int i = 0; i < NK; ++i) {
     const int kk = t + i * NT, k2 = r * C + kk;
-    float2 a[P], w[P];
+    float2 a[P];
 #pragma unroll
     for (int q = 0; q < P; ++q) a[q] = P > 1 ? recv[q * C + kk] : sbuf[spad(k2)];
-    w[0] = make_float2(1.f, 0.f);
 #pragma unroll
-    for (int q = 1; q < P; ++q) {
-      w[q] = __ldg(&p.twiddle[(q - 1) * N2 + k2]);
-      a[q] = cmul(a[q], w[q]);
-    }
+    for (int q = 1; q < P; ++q) a[q] = cmul(a[q], wv[i][q - 1]);
     dft<P>(a);
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) {
       const int k = k2 + N2 * k1;
-      const float2 h = __ldg(&H[k]);
+      const float2 h = hv[i][k1];
       float2 A = cmul(a[k1], make_float2(h.x * sc, h.y * sc));
       if (noise) {
         const float2 g = ase_normal((uint32_t)k, (uint32_t)b, (uint32_t)st.span, p.counter, p.seed_lo, p.seed_hi);
@@ -168,22 +176,22 @@ __device__ __forceinline__ bool ssm_middle(float2* sbuf, float2* recv, uint64_t*
       a[k1] = make_float2(A.x, -A.y);
     }
     dft<P>(a);
+    // Results go out as soon as they are formed: to block q's own slot of
+    // the local sequence (remote store counted on its bars[1]), or in place.
+    if constexpr (P > 1) {
 #pragma unroll
-    for (int q = 0; q < P; ++q) out[i][q] = cmul(a[q], w[q]);
+      for (int q = 0; q < P; ++q) {
+        const float2 o = q == 0 ? a[0] : cmul(a[q], wv[i][q - 1]);
+        const uint32_t dst = mapa_shared(smem_u32(sbuf), q), rbar = mapa_shared(bar1_l, q);
+        st_async_c64(dst + (uint32_t)spad(r * C + kk) * sizeof(float2), o, rbar);
+      }
+    } else {
+      sbuf[spad(kk)] = a[0];
+    }
   }
   if constexpr (P > 1) {
-    const uint32_t bar1_l = smem_u32(&bars[1]);
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const uint32_t dst = mapa_shared(smem_u32(sbuf), q), rbar = mapa_shared(bar1_l, q);
-#pragma unroll
-      for (int i = 0; i < NK; ++i)
-        st_async_c64(dst + (uint32_t)spad(r * C + t + i * NT) * sizeof(float2), out[i][q], rbar);
-    }
     ok = mbar_wait_cluster_bounded(&bars[1], phase, 1 << 20) && ok;
   } else {
-#pragma unroll
-    for (int i = 0; i < NK; ++i) sbuf[spad(t + i * NT)] = out[i][0];
     __syncthreads();
   }
   return ok;
