@@ -26,6 +26,7 @@
 #include "fft.cuh"
 #include "ssm.cuh"
 #include "philox.cuh"
+#include "ldbp_tile.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -72,12 +73,12 @@ __device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict_
     }
     dft<R>(&a[i * R]);
     if constexpr (LAST_OF_INVERSE) {
+      // conjugation completes the inverse transform; then the Kerr step on
+      // the thread's 16 samples (the last pass is always radix 16)
+      static_assert(R == kSsmE && NB == 1, "last inverse pass holds all of the thread's samples");
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        float2 v = make_float2(a[i * R + q].x, -a[i * R + q].y);
-        if (c != 0.f) v = kerr_rotate_precise<true>(v, c);
-        a[i * R + q] = v;
-      }
+      for (int q = 0; q < R; ++q) a[q] = make_float2(a[q].x, -a[q].y);
+      if (c != 0.f) tile_kerr<kSsmE>(a, c);
     }
     const int base = (j - k) * R + k;
 #pragma unroll
