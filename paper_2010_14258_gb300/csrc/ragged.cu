@@ -55,18 +55,18 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-template <int KMAX>
-__device__ __forceinline__ void ragged_step(int K, float2 (&v)[kFwdR], const float4* h, float c, float2* ef,
+template <int KMAX, int R, int NW>
+__device__ __forceinline__ void ragged_step(int K, float2 (&v)[R], const float4* h, float c, float2* ef,
                                             float2* el, int lane, int warp, bool compute) {
   switch (K) {
 #define LDBP_RCASE(k)                                                        \
   case k:                                                                    \
     if constexpr (k <= KMAX) {                                               \
-      float2 xe[kFwdR + 2 * k];                                              \
-      tile_extend<k>(v, xe, ef, el, lane, warp);                             \
+      float2 xe[R + 2 * k];                                                  \
+      tile_extend<k, R, NW>(v, xe, ef, el, lane, warp);                      \
       if (compute) {                                                         \
-        tile_fir<k, false>(xe, h, v);                                        \
-        if (c != 0.f) tile_kerr(v, c);                                       \
+        tile_fir<k, false, R>(xe, h, v);                                     \
+        if (c != 0.f) tile_kerr<R>(v, c);                                    \
       }                                                                      \
     }                                                                        \
     break;
@@ -79,13 +79,16 @@ __device__ __forceinline__ void ragged_step(int K, float2 (&v)[kFwdR], const flo
   }
 }
 
-template <int KMAX>
-__global__ void __launch_bounds__(kFwdNT, KMAX <= 8 ? 2 : 1) ldbp_ragged_kernel(const __grid_constant__ RaggedParams p) {
+// R consecutive samples per thread, NT threads (R * NT = kFwdS samples per tile).
+template <int KMAX, int R, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) ldbp_ragged_kernel(const __grid_constant__ RaggedParams p) {
+  static_assert(R * NT == kFwdS, "tile size");
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);
   float4* taps_s = reinterpret_cast<float4*>(tile + kFwdS);          // [LDBP_MAX_STEPS][KMAX+1]
   float2* edges = reinterpret_cast<float2*>(taps_s + LDBP_MAX_STEPS * (KMAX + 1));  // [2][2][NW][edge]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(edges + 4 * kFwdNW * kFwdEdge);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(edges + 4 * NW * kFwdEdge);
   __shared__ int item_s, K_s[LDBP_MAX_STEPS];
   __shared__ float c_s[LDBP_MAX_STEPS];
   __shared__ int timed_out;
@@ -108,12 +111,12 @@ __global__ void __launch_bounds__(kFwdNT, KMAX <= 8 ? 2 : 1) ldbp_ragged_kernel(
     const RaggedWave w = p.waves[item.wave];
     const long long n = w.n, t0 = (long long)item.tile * w.L;
     const int Lt = (int)min((long long)w.L, n - t0);
-    for (int i = tid; i < w.M; i += kFwdNT) {
+    for (int i = tid; i < w.M; i += NT) {
       K_s[i] = p.K[w.step_off + i];
       c_s[i] = p.c[w.step_off + i];
     }
     __syncthreads();
-    for (int e = tid; e < w.M * (KMAX + 1); e += kFwdNT) {
+    for (int e = tid; e < w.M * (KMAX + 1); e += NT) {
       const int i = e / (KMAX + 1), k = e - i * (KMAX + 1);
       taps_s[e] = tap_pair(k <= K_s[i] ? p.taps[(long long)(w.step_off + i) * p.taps_stride + k]
                                        : make_float2(0.f, 0.f));
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kFwdNT, KMAX <= 8 ? 2 : 1) ldbp_ragged_kernel(
       if (!mbar_wait_bounded(bar, phase)) timed_out = 1;
       phase ^= 1;
     } else {
-      for (int s = tid; s < kFwdS; s += kFwdNT) {
+      for (int s = tid; s < kFwdS; s += NT) {
         long long q = (g0 + s) % n;
         if (q < 0) q += n;
         tile[s] = src[q];
@@ -138,27 +141,27 @@ __global__ void __launch_bounds__(kFwdNT, KMAX <= 8 ? 2 : 1) ldbp_ragged_kernel(
     }
     __syncthreads();
     if (timed_out) break;
-    float2 v[kFwdR];
+    float2 v[R];
     {
-      const float4* t4 = reinterpret_cast<const float4*>(tile + tid * kFwdR);
+      const float4* t4 = reinterpret_cast<const float4*>(tile + tid * R);
 #pragma unroll
-      for (int r = 0; r < kFwdR / 2; ++r) {
+      for (int r = 0; r < R / 2; ++r) {
         const float4 q = t4[r];
         v[2 * r] = make_float2(q.x, q.y);
         v[2 * r + 1] = make_float2(q.z, q.w);
       }
     }
-    const bool compute = warp * 32 * kFwdR < w.L + 2 * w.Hp;
+    const bool compute = warp * 32 * R < w.L + 2 * w.Hp;
     for (int i = 0; i < w.M; ++i) {
       const int K = K_s[i];
-      float2* ef = edges + parity * 2 * kFwdNW * kFwdEdge;
-      ragged_step<KMAX>(K, v, taps_s + i * (KMAX + 1), c_s[i], ef, ef + kFwdNW * kFwdEdge, lane, warp, compute);
+      float2* ef = edges + parity * 2 * NW * kFwdEdge;
+      ragged_step<KMAX, R, NW>(K, v, taps_s + i * (KMAX + 1), c_s[i], ef, ef + NW * kFwdEdge, lane, warp, compute);
       if (K > 0) parity ^= 1;
     }
     {
-      float4* t4 = reinterpret_cast<float4*>(tile + tid * kFwdR);
+      float4* t4 = reinterpret_cast<float4*>(tile + tid * R);
 #pragma unroll
-      for (int r = 0; r < kFwdR / 2; ++r)
+      for (int r = 0; r < R / 2; ++r)
         t4[r] = make_float4(v[2 * r].x, v[2 * r].y, v[2 * r + 1].x, v[2 * r + 1].y);
     }
     float2* dst = p.y + w.offset + t0;
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(kFwdNT, KMAX <= 8 ? 2 : 1) ldbp_ragged_kernel(
       }
     } else {
       __syncthreads();
-      for (int s = tid; s < Lt; s += kFwdNT) dst[s] = tile[w.Hp + s];
+      for (int s = tid; s < Lt; s += NT) dst[s] = tile[w.Hp + s];
       __syncthreads();
     }
     if (tid == 0 && p.done_ns) {
@@ -188,18 +191,25 @@ size_t ragged_smem_bytes(int kmax) {
          sizeof(float4) * (size_t)LDBP_MAX_STEPS * (kmax + 1) + 16;
 }
 
+// Kernel geometry per K_max class: 32 samples per thread in 128-thread blocks,
+// except K <= 2 (16 per thread, 256 threads), as for ldbp_apply's dispatch.
+template <int KMAX> struct RaggedGeom { static constexpr int R = 32, NT = 128, MINB = KMAX <= 4 ? 4 : KMAX <= 8 ? 3 : 2; };
+template <> struct RaggedGeom<2> { static constexpr int R = kFwdR, NT = kFwdNT, MINB = 2; };
+
 template <int KMAX>
 static cudaError_t ragged_prepare(int* blocks_per_sm) {
+  using G = RaggedGeom<KMAX>;
+  auto kern = ldbp_ragged_kernel<KMAX, G::R, G::NT, G::MINB>;
   const size_t smem = ragged_smem_bytes(KMAX);
-  cudaError_t e = cudaFuncSetAttribute(ldbp_ragged_kernel<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ldbp_ragged_kernel<KMAX>, kFwdNT, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, G::NT, smem);
 }
 
 template <int KMAX>
 static cudaError_t ragged_launch(const RaggedParams& p, int grid, cudaStream_t st) {
-  ldbp_ragged_kernel<KMAX><<<grid, kFwdNT, ragged_smem_bytes(KMAX), st>>>(p);
+  using G = RaggedGeom<KMAX>;
+  ldbp_ragged_kernel<KMAX, G::R, G::NT, G::MINB><<<grid, G::NT, ragged_smem_bytes(KMAX), st>>>(p);
   return cudaGetLastError();
 }
 
