@@ -47,6 +47,7 @@ SPAN_KM = 80.0
 FS = 20e9
 POWER_DBM = 2.0
 CHANNEL_STEPS = 100
+E2E_CHUNKS = 12
 
 # FP32 pipe of GB300: 152 SMs x 128 FP32 lanes per clock x 2.07 GHz maximum
 # SM clock, one fused multiply-add = 2 floating-point operations.
@@ -522,11 +523,12 @@ def main():
         ls_sweep[str(T)] = {"samples_steps_per_s": units / (tms / 1e3), "ms": tms, "snr_db": snr_of(z),
                             "frac_fp32": ldbp_flops_per_sample_step(T) * units / (tms / 1e3) / FP32_PEAK_FLOPS}
 
-    # ---- end to end through the public API with pinned host buffers ----
+    # ---- end to end through the C-ABI host-buffer call (pinned host memory) ----
     xh = y.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    pipe = api.HostPipeline(B, N_SAMP, chunks=8)
-    e2e_ms = time_fn(lambda: pipe.run(taps, Ts, cs, xh, yh), max(3, args.steps // 4))
+    ws = torch.empty(api.ldbp_apply_host_workspace(N_SAMP, B), dtype=torch.uint8, device="cuda")
+    e2e_ms = time_fn(lambda: api.ldbp_apply_host(taps, Ts, cs, xh, yh, chunks=E2E_CHUNKS, workspace=ws),
+                     max(3, args.steps // 4))
     nbytes = xh.numel() * 8
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -552,7 +554,7 @@ def main():
                                        "ldbp_ubench measures 3.9e13 FMA/s = 78 TFLOP/s"},
            "clocks": clocks,
            "e2e": {"value": world * units / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                   "d2h_bytes_per_step": nbytes},
+                   "d2h_bytes_per_step": nbytes, "call": f"ldbp_apply_host, {E2E_CHUNKS} chunks, pinned host buffers"},
            "gpu_launches": args.steps,
            "setup_s": setup_s}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -53,6 +53,34 @@ def ldbp_apply(taps, T, c, x, ckpt=None, out=None):
     return y[0] if squeeze else y
 
 
+def ldbp_apply_host_workspace(n, batch) -> int:
+    """Device workspace bytes of ldbp_apply_host for [batch, n] waveforms."""
+    return int(_lib.lib().ldbp_apply_host_workspace(n, batch))
+
+
+def ldbp_apply_host(taps, T, c, x_host, y_host, chunks=8, workspace=None):
+    """ldbp_apply on host (CPU) complex64 [B, n] tensors: chunked copy-in /
+    compute / copy-out overlapped on the library's streams.  Ordered on the
+    current stream; synchronise it before reading y_host.  workspace: a
+    device uint8 tensor of ldbp_apply_host_workspace bytes (allocated if
+    None)."""
+    for name, t in (("x_host", x_host), ("y_host", y_host)):
+        if t.device.type != "cpu" or t.dtype != torch.complex64 or not t.is_contiguous() or t.dim() != 2:
+            raise ValueError(f"{name} must be a contiguous CPU complex64 [B, n] tensor")
+    if x_host.shape != y_host.shape:
+        raise ValueError("x_host and y_host must have the same shape")
+    _check_c64("taps", taps)
+    B, n = x_host.shape
+    need = ldbp_apply_host_workspace(n, B)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    M = len(T)
+    _lib.check(_lib.lib().ldbp_apply_host(_ptr(taps), taps.shape[1], _lib.i32_array(T), _lib.f32_array(c), M,
+                                          x_host.data_ptr(), y_host.data_ptr(), n, B, int(chunks), _ptr(workspace),
+                                          workspace.numel(), _stream()))
+    return y_host
+
+
 def ubench(kind: int) -> float:
     """Measured lane-operation throughput: 0 FP32 FMA, 1 FP32x2 FMA, 2 sine (ops/s)."""
     import ctypes
@@ -276,40 +304,3 @@ class RaggedPlan:
             self.close()
         except Exception:
             pass
-
-
-class HostPipeline:
-    """ldbp_apply on pinned host buffers: the batch is split into chunks whose
-    host->device copy, LDBP pass and device->host copy overlap on three
-    streams (copy-in, compute, copy-out).  Device staging buffers are
-    allocated once per (batch, n)."""
-
-    def __init__(self, batch, n, chunks=8, device="cuda"):
-        self.batch, self.n = batch, n
-        self.chunks = max(1, min(chunks, batch))
-        self.bounds = [round(i * batch / self.chunks) for i in range(self.chunks + 1)]
-        self.xd = torch.empty((batch, n), dtype=torch.complex64, device=device)
-        self.yd = torch.empty_like(self.xd)
-        self.s_in, self.s_cmp, self.s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        self.ev_in = [torch.cuda.Event() for _ in range(self.chunks)]
-        self.ev_cmp = [torch.cuda.Event() for _ in range(self.chunks)]
-
-    def run(self, taps, T, c, x_host, y_host):
-        """x_host, y_host: pinned CPU complex64 [batch, n].  Returns when y_host is filled."""
-        cur = torch.cuda.current_stream()
-        for s in (self.s_in, self.s_cmp, self.s_out):
-            s.wait_stream(cur)
-        for i in range(self.chunks):
-            a, b = self.bounds[i], self.bounds[i + 1]
-            with torch.cuda.stream(self.s_in):
-                self.xd[a:b].copy_(x_host[a:b], non_blocking=True)
-                self.ev_in[i].record(self.s_in)
-            with torch.cuda.stream(self.s_cmp):
-                self.s_cmp.wait_event(self.ev_in[i])
-                ldbp_apply(taps, T, c, self.xd[a:b], out=self.yd[a:b])
-                self.ev_cmp[i].record(self.s_cmp)
-            with torch.cuda.stream(self.s_out):
-                self.s_out.wait_event(self.ev_cmp[i])
-                y_host[a:b].copy_(self.yd[a:b], non_blocking=True)
-        cur.wait_stream(self.s_out)
-        return y_host

@@ -52,3 +52,29 @@ def test_ldbp_apply_rejects(L, kw, needle):
     rc = _apply(L, **kw)
     assert rc == -1
     assert needle in L.ldbp_last_error().decode()
+
+
+def _apply_host(L, **kw):
+    args = dict(x=ctypes.c_void_p(4096), y=ctypes.c_void_p(1 << 22), n=128, B=4, chunks=2,
+                ws=ctypes.c_void_p(1 << 24), wsb=2 * 128 * 4 * 8)
+    args.update(kw)
+    return L.ldbp_apply_host(ctypes.c_void_p(16), 2, _lib.i32_array([3]), _lib.f32_array([-0.1]), 1, args["x"],
+                             args["y"], args["n"], args["B"], args["chunks"], args["ws"], args["wsb"], None)
+
+
+def test_apply_host_workspace_size(L):
+    assert L.ldbp_apply_host_workspace(128, 4) == 2 * 128 * 4 * 8
+    assert L.ldbp_apply_host_workspace(0, 4) == 0
+
+
+@pytest.mark.parametrize("kw, needle", [
+    (dict(x=None), "non-NULL"),
+    (dict(chunks=0), "chunks=0"),
+    (dict(chunks=5), "chunks=5"),
+    (dict(wsb=100), "workspace"),
+    (dict(ws=ctypes.c_void_p((1 << 24) + 8)), "aligned"),
+    (dict(y=ctypes.c_void_p(4096 + 64)), "overlap"),
+])
+def test_ldbp_apply_host_rejects(L, kw, needle):
+    assert _apply_host(L, **kw) == -1
+    assert needle in L.ldbp_last_error().decode()

@@ -145,3 +145,45 @@ def test_full_size_sampled():
         xb = to_np(xd[b])
         ref, floor = fp32_floor(xb, taps, c)
         assert rel_l2(to_np(y[b]), ref) <= max(1e-4, 10 * floor)
+
+
+@pytest.mark.parametrize("phi_max", [0.25, 0.55, 0.78, 3.0, 40.0])
+def test_kerr_step_tiers_elementwise(phi_max):
+    # One Kerr-only step (T = 1, h_0 = 1: the filter is exact) with phases
+    # spread over [0, phi_max]: each warp's largest phase selects the series
+    # of degree 5/6, 7/8, 9/10 or the range-reducing path.  Every sample must
+    # match the FP64 rotation to a few FP32 ulps, plus the FP32 rounding of
+    # the phase itself (about 2^-23 of phi).
+    n = 8192
+    rng = np.random.default_rng(int(phi_max * 100))
+    p = rng.uniform(0.0, 1.0, (2, n))
+    x = c64(np.sqrt(p) * np.exp(2j * np.pi * rng.uniform(size=(2, n))))
+    c = [float(np.float32(phi_max))]
+    taps = [np.array([1.0 + 0j])]
+    y, _ = _run(taps, [1], c, x)
+    ref, _ = oldbp.forward(x, taps, c)
+    err = np.abs(y - ref) / np.maximum(np.abs(ref), 1e-30)
+    assert err.max() <= 4e-7 + 2e-7 * phi_max
+
+
+@pytest.mark.parametrize("chunks,pinned", [(1, True), (3, True), (5, False)])
+def test_apply_host_matches_device_call(chunks, pinned):
+    # the host-buffer call runs the same kernel per chunk of waveforms:
+    # bitwise equal to ldbp_apply on device copies, and to the oracle
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    Ts = [9, 5, 3]
+    taps, c = _model(Ts, seed=11)
+    x = _signal(5, 6000, 12, 4e-3)
+    td = to_dev(_pack(taps))
+    xh = torch.from_numpy(x.astype(np.complex64)).contiguous()
+    yh = torch.zeros_like(xh)
+    if pinned:
+        xh, yh = xh.pin_memory(), yh.pin_memory()
+    api.ldbp_apply_host(td, Ts, c, xh, yh, chunks=chunks)
+    torch.cuda.synchronize()
+    yd = api.ldbp_apply(td, Ts, c, to_dev(x))
+    assert np.array_equal(yh.numpy(), to_np(yd))
+    ref, _ = oldbp.forward(x, taps, c)
+    assert rel_l2(yh.numpy(), ref) <= 1e-4
