@@ -41,6 +41,7 @@ extern "C" {
 #define LDBP_ECUDA (-3)       /* a CUDA runtime call failed */
 #define LDBP_ETIMEOUT (-4)    /* a bounded device wait ran out */
 #define LDBP_EUNSUPPORTED (-5) /* valid request outside what this build supports */
+#define LDBP_ENONFINITE (-6)  /* a NaN or infinite model / fiber parameter */
 
 /* Largest number of LDBP steps per call and largest filter half-width K
  * (filter length T = 2K + 1 <= 33) of the fused LDBP kernels. */
@@ -87,7 +88,8 @@ int ldbp_device_status(void);
  *         receives u_i (the input of step i); ldbp_backward consumes it.
  * Errors: LDBP_EINVAL for NULL x/y/taps/T/c, M out of range, an even or
  * out-of-range T_i, n < 1, batch < 1, overlapping x and y, or a halo sum too
- * large for one tile (2 H > 2048); LDBP_ECUDA if the launch fails.
+ * large for one tile (2 H > 2048); LDBP_ENONFINITE for a NaN or infinite
+ * c_i; LDBP_ECUDA if the launch fails.
  */
 int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
                const void* x, void* y, int64_t n, int32_t batch, void* ckpt, void* stream);
@@ -284,7 +286,8 @@ typedef struct {
  * library-owned device memory (cudaMalloc + synchronous copy); later calls
  * reuse them.
  * Errors: LDBP_EINVAL (NULL pointer, n not a supported power of two,
- * non-positive fs/span/steps/batch, negative alpha); LDBP_ECUDA.
+ * non-positive fs/span/steps/batch, negative alpha); LDBP_ENONFINITE (a NaN
+ * or infinite fiber, link or fs value); LDBP_ECUDA.
  */
 int ssm_forward(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, const void* x, void* y, int64_t n,
                 int32_t batch, void* stream);

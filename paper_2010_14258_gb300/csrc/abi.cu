@@ -1,6 +1,7 @@
 // C ABI entry points: argument validation, tile planning and kernel dispatch.
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -68,7 +69,7 @@ static int check_model(const void* taps, int32_t taps_stride, const int32_t* T, 
     if (K > LDBP_MAX_HALF_TAPS) return fail(LDBP_EINVAL, "T[%d]=%d exceeds the supported length %d", i, t,
                                             2 * LDBP_MAX_HALF_TAPS + 1);
     if (K + 1 > taps_stride) return fail(LDBP_EINVAL, "T[%d]=%d needs taps_stride >= %d", i, t, K + 1);
-    if (!(c[i] == c[i])) return fail(LDBP_EINVAL, "c[%d] is NaN", i);
+    if (!std::isfinite(c[i])) return fail(LDBP_ENONFINITE, "c[%d] is NaN or infinite", i);
     *H += K;
     *kmax = K > *kmax ? K : *kmax;
   }

@@ -202,10 +202,12 @@ static std::string fkey(const ldbp_fiber& f, double fs, long long n) {
 int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x, const void* y, long long n,
                       int batch) {
   if (!f || !l || !x || !y) return fail(LDBP_EINVAL, "fiber, link, x and y must be non-NULL");
-  if (!(fs > 0.0) || !std::isfinite(fs)) return fail(LDBP_EINVAL, "fs_hz must be positive");
+  if (!std::isfinite(fs)) return fail(LDBP_ENONFINITE, "fs_hz is NaN or infinite");
+  if (!(fs > 0.0)) return fail(LDBP_EINVAL, "fs_hz must be positive");
   if (!std::isfinite(f->alpha_db_per_km) || !std::isfinite(f->beta2_ps2_per_km) || !std::isfinite(f->gamma_per_w_km) ||
-      f->alpha_db_per_km < 0)
-    return fail(LDBP_EINVAL, "fiber parameters must be finite (alpha >= 0)");
+      !std::isfinite(l->span_km) || !std::isfinite(l->nf_db) || !std::isfinite(l->carrier_hz))
+    return fail(LDBP_ENONFINITE, "fiber or link parameter is NaN or infinite");
+  if (f->alpha_db_per_km < 0) return fail(LDBP_EINVAL, "alpha must be >= 0");
   if (l->n_spans < 1 || !(l->span_km > 0.0) || l->steps_per_span < 1)
     return fail(LDBP_EINVAL, "link needs n_spans >= 1, span_km > 0, steps_per_span >= 1");
   if (batch < 1) return fail(LDBP_EINVAL, "batch=%d must be >= 1", batch);

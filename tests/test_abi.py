@@ -45,7 +45,6 @@ def _apply(L, **kw):
     (dict(n=0), "n=0"),
     (dict(B=0), "batch=0"),
     (dict(y=ctypes.c_void_p(4096 + 8)), "overlap"),
-    (dict(c=[float("nan")]), "NaN"),
     (dict(ckpt=ctypes.c_void_p(4096 + 512)), "ckpt overlaps"),
 ])
 def test_ldbp_apply_rejects(L, kw, needle):
@@ -78,3 +77,9 @@ def test_apply_host_workspace_size(L):
 def test_ldbp_apply_host_rejects(L, kw, needle):
     assert _apply_host(L, **kw) == -1
     assert needle in L.ldbp_last_error().decode()
+
+
+@pytest.mark.parametrize("v", [float("nan"), float("inf")])
+def test_ldbp_apply_rejects_nonfinite_coefficient(L, v):
+    assert _apply(L, c=[v]) == -6
+    assert "NaN or infinite" in L.ldbp_last_error().decode()

@@ -187,3 +187,25 @@ def test_apply_host_matches_device_call(chunks, pinned):
     assert np.array_equal(yh.numpy(), to_np(yd))
     ref, _ = oldbp.forward(x, taps, c)
     assert rel_l2(yh.numpy(), ref) <= 1e-4
+
+
+def test_remark4_rescaled_model_same_output():
+    # Remark 4 on the CUDA path: filters rescaled by s_i / s_{i-1} and Kerr
+    # coefficients by 1 / |s_i|^2 give the same outputs (to FP32 rounding)
+    Ts = [9] * 12 + [5] * 12 + [3]
+    taps, c = _model(Ts, seed=44)
+    c[-1] = 0.0
+    rng = np.random.default_rng(44)
+    s = [rng.uniform(0.5, 2.0) * np.exp(2j * np.pi * rng.uniform()) for _ in range(len(Ts) - 1)]
+    t2, c2, prev = [], [], 1.0
+    for i, (h, ci) in enumerate(zip(taps, c)):
+        si = s[i] if i < len(s) else 1.0
+        t2.append(c64(np.asarray(h) * si / prev))
+        c2.append(float(np.float32(ci / abs(si) ** 2)))
+        prev = si
+    x = _signal(2, 16384, 45, 3e-3)
+    y1, _ = _run(taps, Ts, c, x)
+    y2, _ = _run(t2, Ts, c2, x)
+    ref, floor = fp32_floor(x, taps, c)
+    assert rel_l2(y1, ref) <= max(1e-4, 10 * floor)
+    assert rel_l2(y2, y1) <= max(1e-4, 10 * floor)

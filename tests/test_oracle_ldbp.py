@@ -199,3 +199,40 @@ def test_loss_gradient_finite_differences():
               - txrx.evaluate(y - eps * d, s, 2, 0.1, P)["loss"]) / (2 * eps)
         an = np.real(np.vdot(gy, d))
         assert abs(fd - an) < 1e-5 * abs(an) + 1e-9
+
+
+def _rescaled(taps, c, s):
+    """Remark 4: scaling the signal before every nonlinear step by s_i and
+    undoing it in the next filter, with c_i / |s_i|^2 in the Kerr step, leaves
+    the model unchanged.  taps/c of M steps, s of M - 1 complex scales."""
+    out_t, out_c, prev = [], [], 1.0
+    for i, (h, ci) in enumerate(zip(taps, c)):
+        si = s[i] if i < len(s) else 1.0
+        out_t.append(np.asarray(h) * si / prev)
+        out_c.append(ci / abs(si) ** 2)
+        prev = si
+    return out_t, out_c
+
+
+def test_overparameterisation_invariance_remark4():
+    # Remark 4: rescaled filters and nonlinear coefficients give the same model;
+    # in particular every coefficient can be normalised to +-1 (last step linear).
+    rng = np.random.default_rng(4)
+    M, n = 5, 257
+    taps = [synth.complex_normal(3 + i % 3, 40 + i, 0.5) for i in range(M)]
+    c = [float(v) for v in rng.uniform(-2.0, 2.0, M - 1)] + [0.0]
+    x = synth.complex_normal(n, 7, 0.7).reshape(1, n)
+    ref, _ = ldbp.forward(x, taps, c)
+    s = [complex(a, b) for a, b in rng.normal(size=(M - 1, 2))]
+    t2, c2 = _rescaled(taps, c, s)
+    y2, _ = ldbp.forward(x, t2, c2)
+    assert np.allclose(y2, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    s_unit = [np.sqrt(abs(ci)) for ci in c[:-1]]
+    t3, c3 = _rescaled(taps, c, s_unit)
+    assert np.allclose(np.abs(c3[:-1]), 1.0) and c3[-1] == 0.0
+    y3, _ = ldbp.forward(x, t3, c3)
+    assert np.allclose(y3, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    # a plausible mistake (rescaling c by |s| instead of |s|^2) breaks it
+    bad = [ci / abs(si) for ci, si in zip(c[:-1], s)] + [0.0]
+    yb, _ = ldbp.forward(x, t2, bad)
+    assert not np.allclose(yb, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
