@@ -77,26 +77,54 @@ __device__ __forceinline__ void tile_fir(const float2 (&xe)[R + 2 * K], const fl
   }
 }
 
-// Taylor coefficients of sin(c p) and cos(c p) as polynomials in the power
-// p = |v|^2 (c folded in): sin = p (s1 + p^2 (s3 + p^2 (s5 + ...))),
-// cos = 1 + p^2 (c2 + p^2 (c4 + ...)).  Computed once per step.
-struct KerrPoly {
-  float s1, s3, s5, s7, s9, c2, c4, c6, c8, c10;
+// exp(j phi) for the Kerr step, phi = c p with p = |v|^2, as polynomials in p
+// with c folded into the coefficients (computed once per step):
+//   sin(phi) = p (s1 + p^2 (s3 + p^2 (s5 + ...))),  cos(phi) = 1 + p^2 (c2 + p^2 (c4 + ...)).
+// The coefficients are minimax approximations (Remez exchange, absolute
+// error) of sin x by odd and cos x - 1 by even polynomials in x:
+//   tier A, |x| <= 0.5: degree 5 / 6, truncation error 2.4e-8 / 8.8e-10;
+//   tier B, |x| <= 1.0: degree 7 / 8, truncation error 1.05e-8 / 6.0e-10;
+// (paper_2010_14258_gb300/kerr_coeffs.py recomputes them).  With FP32
+// evaluation the error stays below one FP32 ulp of 1 (8.6e-8 / 1.2e-7 worst
+// case in an exact emulation of the arithmetic below).
+constexpr float kKerrTierA = 0.5f, kKerrTierB = 1.0f;
+constexpr float kSinA1 = 0.9999996633882672f, kSinA3 = -0.16665588371358184f, kSinA5 = 0.00824692499263815f;
+constexpr float kCosA2 = -0.4999999293270643f, kCosA4 = 0.04166494975184432f, kCosA6 = -0.00137702498229312f;
+constexpr float kSinB1 = 0.9999999054170744f, kSinB3 = -0.1666654029027963f, kSinB5 = 0.0083287710331470845f,
+                kSinB7 = -1.9229923808368593e-4f;
+constexpr float kCosB2 = -0.49999998116466243f, kCosB4 = 0.041666483357827591f, kCosB6 = -0.0013883339760550355f,
+                kCosB8 = 2.413824676776131e-5f;
+
+struct KerrPolyA {
+  float s1, s3, s5, c2, c4, c6;
+};
+struct KerrPolyB {
+  float s1, s3, s5, s7, c2, c4, c6, c8;
 };
 
-__device__ __forceinline__ KerrPoly kerr_poly(float c) {
-  KerrPoly k;
-  const float c2 = c * c;
-  k.s1 = c;
-  k.s3 = k.s1 * c2 * -1.66666666666666667e-1f;  // / (2 * 3)
-  k.s5 = k.s3 * c2 * -5.0e-2f;                  // / (4 * 5)
-  k.s7 = k.s5 * c2 * -2.38095238095238095e-2f;  // / (6 * 7)
-  k.s9 = k.s7 * c2 * -1.38888888888888889e-2f;  // / (8 * 9)
-  k.c2 = c2 * -0.5f;
-  k.c4 = k.c2 * c2 * -8.33333333333333333e-2f;  // / (3 * 4)
-  k.c6 = k.c4 * c2 * -3.33333333333333333e-2f;  // / (5 * 6)
-  k.c8 = k.c6 * c2 * -1.78571428571428571e-2f;  // / (7 * 8)
-  k.c10 = k.c8 * c2 * -1.11111111111111111e-2f; // / (9 * 10)
+__device__ __forceinline__ KerrPolyA kerr_poly_a(float c) {
+  const float c2 = c * c, c3 = c2 * c, c4 = c2 * c2;
+  KerrPolyA k;
+  k.s1 = kSinA1 * c;
+  k.s3 = kSinA3 * c3;
+  k.s5 = kSinA5 * (c4 * c);
+  k.c2 = kCosA2 * c2;
+  k.c4 = kCosA4 * c4;
+  k.c6 = kCosA6 * (c4 * c2);
+  return k;
+}
+
+__device__ __forceinline__ KerrPolyB kerr_poly_b(float c) {
+  const float c2 = c * c, c3 = c2 * c, c4 = c2 * c2, c6 = c4 * c2;
+  KerrPolyB k;
+  k.s1 = kSinB1 * c;
+  k.s3 = kSinB3 * c3;
+  k.s5 = kSinB5 * (c4 * c);
+  k.s7 = kSinB7 * (c6 * c);
+  k.c2 = kCosB2 * c2;
+  k.c4 = kCosB4 * c4;
+  k.c6 = kCosB6 * c6;
+  k.c8 = kCosB8 * (c4 * c4);
   return k;
 }
 
@@ -112,9 +140,8 @@ __device__ __forceinline__ float tile_power(const float2 (&v)[R], float (&p)[R])
   return m;
 }
 
-// (cos, sin)(c p) for two powers at once, |c p| <= 0.3: series truncated after
-// (c p)^5 / (c p)^6 (truncation below 4.4e-8 / 1.7e-9, under half an FP32 ulp of 1).
-__device__ __forceinline__ void kerr_pair_small(float2 P, const KerrPoly& k, float2& cs, float2& sn) {
+// (cos, sin)(c p) for two powers at once (packed FP32x2), tier A.
+__device__ __forceinline__ void kerr_pair_a(float2 P, const KerrPolyA& k, float2& cs, float2& sn) {
   const float2 r2 = __fmul2_rn(P, P);
   float2 t = __ffma2_rn(r2, make_float2(k.s5, k.s5), make_float2(k.s3, k.s3));
   t = __ffma2_rn(r2, t, make_float2(k.s1, k.s1));
@@ -124,8 +151,8 @@ __device__ __forceinline__ void kerr_pair_small(float2 P, const KerrPoly& k, flo
   cs = __ffma2_rn(r2, u, make_float2(1.f, 1.f));
 }
 
-// |c p| <= 0.6: series to (c p)^7 / (c p)^8 (truncation below 2.9e-8 / 1.8e-9).
-__device__ __forceinline__ void kerr_pair_mid(float2 P, const KerrPoly& k, float2& cs, float2& sn) {
+// The same, tier B.
+__device__ __forceinline__ void kerr_pair_b(float2 P, const KerrPolyB& k, float2& cs, float2& sn) {
   const float2 r2 = __fmul2_rn(P, P);
   float2 t = __ffma2_rn(r2, make_float2(k.s7, k.s7), make_float2(k.s5, k.s5));
   t = __ffma2_rn(r2, t, make_float2(k.s3, k.s3));
@@ -137,46 +164,26 @@ __device__ __forceinline__ void kerr_pair_mid(float2 P, const KerrPoly& k, float
   cs = __ffma2_rn(r2, u, make_float2(1.f, 1.f));
 }
 
-// The same for |c p| <= pi/4 (series to (c p)^9 / (c p)^10, error below 2e-9).
-__device__ __forceinline__ void kerr_pair(float2 P, const KerrPoly& k, float2& cs, float2& sn) {
-  const float2 r2 = __fmul2_rn(P, P);
-  float2 t = __ffma2_rn(r2, make_float2(k.s9, k.s9), make_float2(k.s7, k.s7));
-  t = __ffma2_rn(r2, t, make_float2(k.s5, k.s5));
-  t = __ffma2_rn(r2, t, make_float2(k.s3, k.s3));
-  t = __ffma2_rn(r2, t, make_float2(k.s1, k.s1));
-  sn = __fmul2_rn(P, t);
-  float2 u = __ffma2_rn(r2, make_float2(k.c10, k.c10), make_float2(k.c8, k.c8));
-  u = __ffma2_rn(r2, u, make_float2(k.c6, k.c6));
-  u = __ffma2_rn(r2, u, make_float2(k.c4, k.c4));
-  u = __ffma2_rn(r2, u, make_float2(k.c2, k.c2));
-  cs = __ffma2_rn(r2, u, make_float2(1.f, 1.f));
-}
-
-// Phase tiers of the Kerr step, chosen per warp from its largest phase
-// |c p|: the usual per-step nonlinear phase is well below 0.3.
-constexpr float kKerrTierA = 0.3f, kKerrTierB = 0.6f, kKerrTierC = 0.785398163f;
-
-// e[r] = exp(j c |v[r]|^2).  Packed FP32x2 Taylor series in p for
-// |c p| <= 0.3, 0.6 and pi/4 (tiers A, B, C), the range-reducing scalar path
-// (expj) beyond; every path is accurate to about one FP32 ulp.
+// e[r] = exp(j c |v[r]|^2).  The tier is chosen per warp from its largest
+// phase |c p|: tier A (the usual per-step nonlinear phase), tier B, and the
+// range-reducing scalar path (expj) beyond |c p| = 1.
 template <int R = kFwdR>
 __device__ __forceinline__ void tile_expj(const float2 (&v)[R], float c, float2 (&e)[R]) {
   float p[R];
   const float m = tile_power(v, p) * fabsf(c);
-  const KerrPoly k = kerr_poly(c);
-#define LDBP_EXPJ_TIER(fn)                                 \
-  _Pragma("unroll") for (int r = 0; r < R; r += 2) {   \
+#define LDBP_EXPJ_TIER(fn, k)                              \
+  _Pragma("unroll") for (int r = 0; r < R; r += 2) {       \
     float2 cc, ss;                                         \
     fn(make_float2(p[r], p[r + 1]), k, cc, ss);            \
     e[r] = make_float2(cc.x, ss.x);                        \
     e[r + 1] = make_float2(cc.y, ss.y);                    \
   }
   if (__all_sync(0xffffffffu, m <= kKerrTierA)) {
-    LDBP_EXPJ_TIER(kerr_pair_small)
+    const KerrPolyA k = kerr_poly_a(c);
+    LDBP_EXPJ_TIER(kerr_pair_a, k)
   } else if (__all_sync(0xffffffffu, m <= kKerrTierB)) {
-    LDBP_EXPJ_TIER(kerr_pair_mid)
-  } else if (__all_sync(0xffffffffu, m <= kKerrTierC)) {
-    LDBP_EXPJ_TIER(kerr_pair)
+    const KerrPolyB k = kerr_poly_b(c);
+    LDBP_EXPJ_TIER(kerr_pair_b, k)
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) e[r] = expj<true>(c * p[r]);
@@ -190,20 +197,19 @@ template <int R = kFwdR>
 __device__ __forceinline__ void tile_kerr(float2 (&v)[R], float c) {
   float p[R];
   const float m = tile_power(v, p) * fabsf(c);
-  const KerrPoly k = kerr_poly(c);
-#define LDBP_KERR_TIER(fn)                                                                                  \
-  _Pragma("unroll") for (int r = 0; r < R; r += 2) {                                                    \
+#define LDBP_KERR_TIER(fn, k)                                                                               \
+  _Pragma("unroll") for (int r = 0; r < R; r += 2) {                                                        \
     float2 cc, ss;                                                                                          \
     fn(make_float2(p[r], p[r + 1]), k, cc, ss);                                                             \
     v[r] = make_float2(fmaf(v[r].x, cc.x, -v[r].y * ss.x), fmaf(v[r].x, ss.x, v[r].y * cc.x));              \
     v[r + 1] = make_float2(fmaf(v[r + 1].x, cc.y, -v[r + 1].y * ss.y), fmaf(v[r + 1].x, ss.y, v[r + 1].y * cc.y)); \
   }
   if (__all_sync(0xffffffffu, m <= kKerrTierA)) {
-    LDBP_KERR_TIER(kerr_pair_small)
+    const KerrPolyA k = kerr_poly_a(c);
+    LDBP_KERR_TIER(kerr_pair_a, k)
   } else if (__all_sync(0xffffffffu, m <= kKerrTierB)) {
-    LDBP_KERR_TIER(kerr_pair_mid)
-  } else if (__all_sync(0xffffffffu, m <= kKerrTierC)) {
-    LDBP_KERR_TIER(kerr_pair)
+    const KerrPolyB k = kerr_poly_b(c);
+    LDBP_KERR_TIER(kerr_pair_b, k)
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = cmul(v[r], expj<true>(c * p[r]));

@@ -147,11 +147,11 @@ def test_full_size_sampled():
         assert rel_l2(to_np(y[b]), ref) <= max(1e-4, 10 * floor)
 
 
-@pytest.mark.parametrize("phi_max", [0.25, 0.55, 0.78, 3.0, 40.0])
+@pytest.mark.parametrize("phi_max", [0.25, 0.49, 0.75, 0.99, 3.0, 40.0])
 def test_kerr_step_tiers_elementwise(phi_max):
     # One Kerr-only step (T = 1, h_0 = 1: the filter is exact) with phases
     # spread over [0, phi_max]: each warp's largest phase selects the series
-    # of degree 5/6, 7/8, 9/10 or the range-reducing path.  Every sample must
+    # of degree 5/6 (|phase| <= 0.5), 7/8 (<= 1) or the range-reducing path.  Every sample must
     # match the FP64 rotation to a few FP32 ulps, plus the FP32 rounding of
     # the phase itself (about 2^-23 of phi).
     n = 8192
