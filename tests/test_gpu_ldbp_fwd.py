@@ -129,12 +129,14 @@ def test_linear_only_layers_and_large_phase():
         assert rel_l2(y, ref) <= 1e-5 * 10
 
 
-def test_full_size_sampled():
-    # 256 x 65536 at M = 25, T = 3: compare sampled waveforms, full length
+@pytest.mark.parametrize("T", [3, 9, 15])
+def test_full_size_sampled(T):
+    # the benchmark's launch: 256 x 65536 at M = 25 (fixed-width instances);
+    # compare sampled waveforms over their full length
     import torch
     from paper_2010_14258_gb300 import api
     gpu_lib()
-    Ts = [3] * 25
+    Ts = [T] * 25
     taps, c = _model(Ts, seed=2)
     B, n = 256, 65536
     g = torch.Generator(device="cuda").manual_seed(0)
