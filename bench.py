@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=B, help="waveforms per GPU (profiling runs use fewer)")
     ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft", "ldbp_bwd", "channel"],
                     help="run only this kernel (warmup + steps launches) on random input, for ncu captures")
-    ap.add_argument("--workload", default="ldbp", choices=["ldbp", "channel", "ragged", "train"],
+    ap.add_argument("--workload", default="ldbp", choices=["ldbp", "channel", "ragged", "train", "sym32"],
                     help="ldbp: the headline; channel / ragged / train: the other workloads, reported separately")
     return ap.parse_args()
 
@@ -396,6 +396,49 @@ def workload_train(args, api):
                       "taps_after": int(sum(tr.T))}))
 
 
+def workload_sym32(args, api):
+    """Symmetric-SSM-based LDBP with logarithmic step sizes (Sec. IV-C) at 32 GBd, T = 31 (2 StPS) and 21 (4 StPS):
+    256 x 65536 samples (2 samples/symbol, fs = 64 GHz), 10 x 100 km at 4 dBm, data from
+    the GPU channel (50 symmetric steps/span, ASE).  LS-initialised LDBP with 2 StPS
+    (l = 21 layers) and 4 StPS (l = 41), against symmetric FD DBP with 2 and 4 uniform StPS
+    and linear compensation (gamma = 0), all on the same waveforms."""
+    import torch
+    import synth
+    from paper_2010_14258_gb300 import init
+    Bw, nsym, fs, nsp, lsp, pdbm = args.batch, 32768, 64e9, 10, 100.0, 4.0
+    n = 2 * nsym
+    fib = synth.Fiber()
+    sym = torch.from_numpy(synth.qam16_symbols(Bw, nsym, 3000).astype(np.complex64)).cuda()
+    pw = torch.full((Bw,), 1e-3 * 10 ** (pdbm / 10), dtype=torch.float32, device="cuda")
+    x = api.tx(sym, pw)
+    y = api.ssm_forward(fib, synth.Link(nsp, lsp, 50, True, True, 5.0, 1.946e14, seed=91, counter=0), fs, x, out=x)
+    z = torch.empty_like(y)
+
+    def snr_of(out):
+        st, _, _ = api.rx(out, sym, pw)
+        return api.snr_db(st)
+
+    res = {}
+    lin = synth.Fiber(fib.alpha_db_per_km, fib.beta2_ps2_per_km, 0.0)
+    api.dbp_apply(lin, synth.Link(nsp, lsp, 1, True, False), fs, y, steps_per_span=1, symmetric=True, out=z)
+    res["linear_cd_snr_db"] = snr_of(z)
+    for stps, T in ((2, 31), (4, 21)):
+        link = synth.Link(nsp, lsp, stps, True, False)
+        dms = time_fn(lambda: api.dbp_apply(fib, link, fs, y, steps_per_span=stps, symmetric=True, out=z), 5, 1)
+        res[f"fd_dbp_{stps}stps"] = {"snr_db": snr_of(z), "ms": dms}
+        taps, c = init.ldbp_init_symmetric(T, nsp, lsp, fs, steps_per_span=stps)
+        tp = pack_taps(taps, M=len(taps))
+        Ts, cs = [T] * len(taps), [float(v) for v in c]
+        ms = time_fn(lambda: api.ldbp_apply(tp, Ts, cs, y, out=z), 20, 3)
+        units = Bw * n * len(Ts)
+        res[f"ldbp_{stps}stps_T{T}"] = {
+            "layers": len(Ts), "snr_db": snr_of(z), "ms": ms, "samples_steps_per_s": units / (ms / 1e3),
+            "frac_fp32": ldbp_flops_per_sample_step(T) * units / (ms / 1e3) / FP32_PEAK_FLOPS,
+            "speedup_vs_fd_dbp_same_stps": dms / ms}
+    print(json.dumps({"workload": f"ldbp_symmetric_logsteps_32gbd_{Bw}x{n}_10x100km", "unit": UNIT,
+                      "model": "LS-initialised (untrained)", **res}))
+
+
 def train_model(T: int, iters: int, rank: int):
     """Train LDBP with filter length T on the GPU on short frames of the same link."""
     from paper_2010_14258_gb300.train import Trainer, TrainConfig
@@ -435,6 +478,8 @@ def main():
         return workload_ragged(args, api)
     if args.workload == "train":
         return workload_train(args, api)
+    if args.workload == "sym32":
+        return workload_sym32(args, api)
 
     fib = synth.Fiber()
     t_setup = time.perf_counter()

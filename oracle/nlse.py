@@ -37,7 +37,8 @@ Readings (the paper is silent or ambiguous):
 Parity pins (tests/test_oracle_nlse.py): gamma = 0 closed form, beta2 = 0
 closed form, alpha = 0 energy conservation, DBP-of-forward identity on the
 same grid, fundamental soliton, symmetric O(M^-2) / asymmetric O(M^-1)
-convergence, ASE variance formula.
+convergence, ASE variance formula; DBP with explicit (non-uniform) steps:
+beta2 = 0 and gamma = 0 closed forms for any step sizes.
 """
 from __future__ import annotations
 
@@ -163,6 +164,34 @@ def dbp(y, fiber, link, fs: float, steps_per_span: int, symmetric: bool):
     for _ in range(link.n_spans):
         u = u / gain
         for _ in range(N):
+            if symmetric:
+                u = linear_step(u, -beta2, -alpha, d / 2.0, fs)
+                u = kerr(u, -gamma * lmid(alpha, d))
+                u = linear_step(u, -beta2, -alpha, d / 2.0, fs)
+            else:
+                u = linear_step(u, -beta2, -alpha, d, fs)
+                u = kerr(u, -gamma * leff(alpha, d))
+    return u[0] if squeeze else u
+
+
+def dbp_steps(y, fiber, n_spans: int, span_km: float, steps_km, fs: float, symmetric: bool):
+    """DBP (Sec. IV) with explicit step sizes: steps_km lists the steps of one
+    span in DBP order (the first step starts at the span end, where the
+    amplifier gain has been undone); every span uses the same list.  With
+    steps_km = [L_sp / N] * N this is ``dbp``.  Non-uniform steps are the
+    logarithmic step sizes of Sec. IV-C (Example 1).
+    """
+    u = np.array(y, dtype=np.complex128, copy=True)
+    squeeze = u.ndim == 1
+    if squeeze:
+        u = u[None, :]
+    alpha, beta2, gamma = si_alpha(fiber.alpha_db_per_km), si_beta2(fiber.beta2_ps2_per_km), si_gamma(fiber.gamma_per_w_km)
+    Lsp = span_km * 1e3
+    gain = np.exp(alpha * Lsp / 2.0)
+    for _ in range(n_spans):
+        u = u / gain
+        for dk in steps_km:
+            d = dk * 1e3
             if symmetric:
                 u = linear_step(u, -beta2, -alpha, d / 2.0, fs)
                 u = kerr(u, -gamma * lmid(alpha, d))

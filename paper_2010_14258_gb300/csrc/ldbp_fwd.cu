@@ -187,10 +187,10 @@ static cudaError_t launch_cls(const FwdParams& p, int grid, cudaStream_t st) {
 }
 
 // Kernel instance for a model.  Uniform filter widths of the usual models
-// (T = 3, 5, 7, 9, 15) get fixed-width instances, mixed widths the per-step
+// (T = 3, 5, 7, 9, 15, 21, 31) get fixed-width instances, mixed widths the per-step
 // dispatch.  32 samples per thread in 128-thread blocks except where the
 // per-step dispatch over K <= 2 (or up to 16) runs faster with 16 per thread.
-enum FwdInstance { kFix1, kFix2, kFix3, kFix4, kFix7, kGen2, kGen4, kGen8, kGen16 };
+enum FwdInstance { kFix1, kFix2, kFix3, kFix4, kFix7, kFix10, kFix15, kGen2, kGen4, kGen8, kGen16 };
 
 static FwdInstance fwd_select(const int* K, int M, int kmax_needed) {
   bool uniform = true;
@@ -202,6 +202,8 @@ static FwdInstance fwd_select(const int* K, int M, int kmax_needed) {
       case 3: return kFix3;
       case 4: return kFix4;
       case 7: return kFix7;
+      case 10: return kFix10;
+      case 15: return kFix15;
       default: break;
     }
   }
@@ -228,6 +230,8 @@ cudaError_t launch_ldbp_fwd(const FwdParams& p, int kmax_needed, cudaStream_t st
     case kFix3: return launch_cls<4, 4, 3, 32, 128>(p, grid, st);
     case kFix4: return launch_cls<4, 4, 4, 32, 128>(p, grid, st);
     case kFix7: return launch_cls<8, 3, 7, 32, 128>(p, grid, st);
+    case kFix10: return launch_cls<16, 2, 10, 32, 128>(p, grid, st);
+    case kFix15: return launch_cls<16, 2, 15, 32, 128>(p, grid, st);
     case kGen2: return launch_cls<2, 3, -1>(p, grid, st);
     case kGen4: return launch_cls<4, 4, -1, 32, 128>(p, grid, st);
     case kGen8: return launch_cls<8, 3, -1, 32, 128>(p, grid, st);

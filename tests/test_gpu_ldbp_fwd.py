@@ -211,3 +211,20 @@ def test_remark4_rescaled_model_same_output():
     ref, floor = fp32_floor(x, taps, c)
     assert rel_l2(y1, ref) <= max(1e-4, 10 * floor)
     assert rel_l2(y2, y1) <= max(1e-4, 10 * floor)
+
+
+@pytest.mark.parametrize("stps,T", [(2, 15), (4, 9)])
+def test_symmetric_log_step_ldbp_parity(stps, T):
+    # symmetric-SSM-based LDBP with logarithmic steps (Sec. IV-C) at 32 GBd,
+    # 2 samples per symbol, 10 x 100 km: l = 10 * StPS + 1 layers, the last
+    # one linear-only, layer gains != 1
+    from paper_2010_14258_gb300 import init
+    taps, c = init.ldbp_init_symmetric(T, 10, 100.0, 64e9, steps_per_span=stps)
+    taps = [c64(h) for h in taps]
+    c = [float(np.float32(v)) for v in c]
+    Ts = [T] * len(taps)
+    assert len(Ts) == 10 * stps + 1 and c[-1] == 0.0
+    x = _signal(2, 16384, 50 + stps, 1e-3 * 10 ** 0.4)
+    y, _ = _run(taps, Ts, c, x)
+    ref, floor = fp32_floor(x, taps, c)
+    assert rel_l2(y, ref) <= max(1e-4, 10 * floor)

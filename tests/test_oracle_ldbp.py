@@ -236,3 +236,36 @@ def test_overparameterisation_invariance_remark4():
     bad = [ci / abs(si) for ci, si in zip(c[:-1], s)] + [0.0]
     yb, _ = ldbp.forward(x, t2, bad)
     assert not np.allclose(yb, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+
+
+def test_log_step_sizes_and_layers_example1():
+    # Example 1: L_sp = 100 km, 2 spans, symmetric SSM with 2 StPS: logarithmic
+    # steps of about 70 and 30 km, merged layer lengths 35, 50, 50, 50, 15 km
+    from paper_2010_14258_gb300 import init
+    d = init.log_step_sizes(100.0, 2)
+    assert abs(d[0] - 70) < 0.5 and abs(d[1] - 30) < 0.5 and abs(sum(d) - 100.0) < 1e-9
+    dp, g, c = init.symmetric_layers(2, 100.0, d)
+    assert len(dp) == 5 and np.allclose(dp, [35, 50, 50, 50, 15], atol=0.5)
+    assert np.isclose(dp[1], dp[2]) and np.isclose(dp[2], dp[3]) and c[-1] == 0.0
+    # the gains of a span (and its amplifier) multiply to one
+    assert np.isclose(np.prod(g), 1.0)
+    # uniform steps: plain halving and merging
+    assert init.log_step_sizes(80.0, 4, zeta=0.0) == [20.0] * 4
+
+
+@pytest.mark.parametrize("log_steps", [True, False])
+def test_symmetric_ldbp_layers_equal_symmetric_dbp(log_steps):
+    # With exact full-length filters (T = n odd), the symmetric-SSM-based LDBP
+    # built from symmetric_layers (l = M + 1 layers: merged half-steps, gains,
+    # c = -gamma l_mid, last layer linear) is symmetric DBP with the same steps.
+    from paper_2010_14258_gb300 import init
+    n, fs, N, L, K = 255, 64e9, 3, 100.0, 2
+    fib = synth.Fiber()
+    steps = init.log_step_sizes(L, K) if log_steps else [L / K] * K
+    y = synth.gaussian_waveform(2, n, 17, 4e-3)
+    ref = nlse.dbp_steps(y, fib, N, L, steps, fs, True)
+    dp, g, c = init.symmetric_layers(N, L, steps)
+    b2 = nlse.si_beta2(fib.beta2_ps2_per_km)
+    taps = [gi * ldbp.dbp_taps_full(n, -b2 * d * 1e3 * fs ** 2 / 2) for d, gi in zip(dp, g)]
+    out, _ = ldbp.forward(y, taps, c)
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-11

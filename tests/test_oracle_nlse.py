@@ -170,3 +170,31 @@ def test_ase_noise_variance_and_whiteness():
     y = nlse.channel(x, _fiber(beta2=0.0, gamma=0.0), link, fs)
     ref = sum(nlse.ase_noise(8192, 4, s, s2, 99, 0) for s in range(3))
     assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-12
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_dbp_explicit_steps_closed_forms(symmetric):
+    # Non-uniform steps (70.4 / 29.6 km, the logarithmic sizes of Example 1):
+    # beta2 = 0 must give the exact SPM inverse y exp(-j N gamma L_eff(L_sp) |y|^2)
+    # for any step sizes (the loss integrals telescope); gamma = 0 the exact
+    # all-pass dispersion inverse; uniform steps must equal dbp().
+    class F:
+        def __init__(self, a, b, g):
+            self.alpha_db_per_km, self.beta2_ps2_per_km, self.gamma_per_w_km = a, b, g
+    n, fs, N, L = 256, 20e9, 3, 100.0
+    steps = [70.42, 29.58]
+    y = synth.gaussian_waveform(2, n, 31, 5e-3)
+    f0 = F(0.2, 0.0, 1.3)
+    out = nlse.dbp_steps(y, f0, N, L, steps, fs, symmetric)
+    a = nlse.si_alpha(0.2)
+    ref = y * np.exp(-1j * N * nlse.si_gamma(1.3) * nlse.leff(a, L * 1e3) * np.abs(y) ** 2)
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(y))
+    f1 = F(0.2, -21.7, 0.0)
+    out = nlse.dbp_steps(y, f1, N, L, steps, fs, symmetric)
+    w = nlse.omega_grid(n, fs)
+    ref = np.fft.ifft(np.fft.fft(y, axis=-1) * np.exp(1j * (-nlse.si_beta2(-21.7) / 2) * w ** 2 * N * L * 1e3), axis=-1)
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(y))
+    fib = synth.Fiber()
+    link = synth.Link(N, L, 4, symmetric, False)
+    assert np.allclose(nlse.dbp_steps(y, fib, N, L, [L / 4] * 4, fs, symmetric),
+                       nlse.dbp(y, fib, link, fs, 4, symmetric), rtol=0, atol=1e-14)
