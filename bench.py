@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=B, help="waveforms per GPU (profiling runs use fewer)")
     ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft", "ldbp_bwd", "channel"],
                     help="run only this kernel (warmup + steps launches) on random input, for ncu captures")
-    ap.add_argument("--workload", default="ldbp", choices=["ldbp", "channel", "ragged", "train", "sym32"],
+    ap.add_argument("--workload", default="ldbp", choices=["ldbp", "channel", "ragged", "train", "sym32", "essm"],
                     help="ldbp: the headline; channel / ragged / train: the other workloads, reported separately")
     return ap.parse_args()
 
@@ -439,6 +439,48 @@ def workload_sym32(args, api):
                       "model": "LS-initialised (untrained)", **res}))
 
 
+def workload_essm(args, api):
+    """Learned enhanced SSM (filtered nonlinear steps, Sec. III-C): the LDBP inference
+    workload (256 x 65536, 25 x 80 km at 2 dBm, GPU channel data) with a (2 kappa + 1)-tap
+    real filter on |v|^2 in every nonlinear step; T = 9, kappa in {0, 8, 20}, unit-filter
+    and low-pass initialisations; throughput, FP32 fraction of the direct-form work
+    (8T + 9 + 2(2 kappa + 1) flops per sample-step) and effective SNR."""
+    import torch
+    import synth
+    fib = synth.Fiber()
+    Bw = args.batch
+    sym = torch.from_numpy(synth.qam16_symbols(Bw, NSYM, 2000).astype(np.complex64)).cuda()
+    pw = torch.full((Bw,), 1e-3 * 10 ** (POWER_DBM / 10), dtype=torch.float32, device="cuda")
+    x = api.tx(sym, pw)
+    y = api.ssm_forward(fib, synth.Link(M_STEPS, SPAN_KM, CHANNEL_STEPS, True, True, 5.0, 1.946e14, seed=77,
+                                        counter=0), FS, x, out=x)
+    z = torch.empty_like(y)
+    T = 9
+    taps_np, c = ls_model(T)
+    tp = pack_taps(taps_np)
+    res = {}
+    for kappa in (0, 8, 20):
+        for init_kind in (("unit",) if kappa == 0 else ("unit", "lowpass")):
+            e = np.zeros((M_STEPS, 2 * kappa + 1), np.float32)
+            if init_kind == "unit":
+                e[:, kappa] = 1.0
+            else:
+                t = np.arange(-kappa, kappa + 1)
+                g = np.exp(-0.5 * (t / (kappa / 4.0)) ** 2)
+                e[:] = g / g.sum()
+            ed = torch.from_numpy(e).cuda()
+            ks = [kappa] * M_STEPS
+            ms = time_fn(lambda: api.ldbp_essm_apply(tp, [T] * M_STEPS, c, ed, ks, y, out=z), 20, 3)
+            st, _, _ = api.rx(z, sym, pw)
+            units = Bw * N_SAMP * M_STEPS
+            flops = (8 * T + 9 + 2 * (2 * kappa + 1)) * units
+            res[f"kappa{kappa}_{init_kind}"] = {"ms": ms, "samples_steps_per_s": units / (ms / 1e3),
+                                                "frac_fp32": flops / (ms / 1e3) / FP32_PEAK_FLOPS,
+                                                "snr_db": api.snr_db(st)}
+    print(json.dumps({"workload": f"ldbp_essm_{Bw}x{N_SAMP}_M{M_STEPS}_T{T}", "unit": UNIT,
+                      "model": "LS-initialised FIR steps (untrained)", **res}))
+
+
 def train_model(T: int, iters: int, rank: int):
     """Train LDBP with filter length T on the GPU on short frames of the same link."""
     from paper_2010_14258_gb300.train import Trainer, TrainConfig
@@ -480,6 +522,8 @@ def main():
         return workload_train(args, api)
     if args.workload == "sym32":
         return workload_sym32(args, api)
+    if args.workload == "essm":
+        return workload_essm(args, api)
 
     fib = synth.Fiber()
     t_setup = time.perf_counter()

@@ -95,6 +95,28 @@ int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const fl
                const void* x, void* y, int64_t n, int32_t batch, void* ckpt, void* stream);
 
 /*
+ * ldbp_essm_apply -- learned enhanced SSM (filtered DBP, Sec. III-C,
+ * Eqs. (9)-(10)): ldbp_apply whose nonlinear steps rotate by a filtered power,
+ *   u_{i+1,j} = v_j exp(j c_i sum_{k=-kappa_i}^{kappa_i} eta^(i)_k |v_{j-k}|^2),
+ *   v = A_i u_i (the symmetric circular FIR of ldbp_apply), indices mod n.
+ * With kappa_i = 0 and eta^(i) = (1) this is ldbp_apply.
+ *
+ *  taps, taps_stride, T, c, M, x, y, n, batch   as for ldbp_apply, except
+ *         T_i <= 2 * LDBP_ESSM_MAX_HALF_TAPS + 1.
+ *  eta    device, float [M][eta_stride]: row i holds the real filter
+ *         eta^(i)_{-kappa_i} .. eta^(i)_{kappa_i} (2 kappa_i + 1 values).
+ *  kappa  host, int32 [M]: 0 <= kappa_i <= LDBP_ESSM_MAX_KAPPA.
+ * The tile halo is sum_i (K_i + kappa_i) per side.
+ * Errors: LDBP_EINVAL (as ldbp_apply; kappa out of range; eta_stride too
+ * small); LDBP_ENONFINITE for a NaN or infinite c_i; LDBP_ECUDA.
+ */
+#define LDBP_ESSM_MAX_KAPPA 24
+#define LDBP_ESSM_MAX_HALF_TAPS 8
+int ldbp_essm_apply(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, const float* eta,
+                    int32_t eta_stride, const int32_t* kappa, int32_t M, const void* x, void* y, int64_t n,
+                    int32_t batch, void* stream);
+
+/*
  * ldbp_apply_host -- ldbp_apply on waveforms in HOST memory (the receiver's
  * end-to-end call): the batch is cut into `chunks` groups of waveforms whose
  * host->device copy, LDBP pass (the computation of ldbp_apply, Eq. (7)) and

@@ -53,6 +53,27 @@ def ldbp_apply(taps, T, c, x, ckpt=None, out=None):
     return y[0] if squeeze else y
 
 
+def ldbp_essm_apply(taps, T, c, eta, kappa, x, out=None):
+    """Learned enhanced SSM (filtered nonlinear steps, Sec. III-C): ldbp_apply whose
+    Kerr phase uses sum_k eta_k |v_{j-k}|^2.  eta: device float32 [M, stride] with
+    row i = (eta_{-kappa_i}, ..., eta_{kappa_i}); kappa: per-step half-widths."""
+    squeeze = x.dim() == 1
+    x2 = x.unsqueeze(0) if squeeze else x
+    _check_c64("x", x2)
+    _check_c64("taps", taps)
+    if eta.dtype != torch.float32 or not eta.is_cuda or not eta.is_contiguous() or eta.dim() != 2:
+        raise ValueError("eta must be a contiguous CUDA float32 [M, stride] tensor")
+    B, n = x2.shape
+    M = len(T)
+    if taps.shape[0] != M or eta.shape[0] != M or len(kappa) != M:
+        raise ValueError("taps, eta and kappa need M = len(T) rows")
+    y = torch.empty_like(x2) if out is None else out
+    _lib.check(_lib.lib().ldbp_essm_apply(_ptr(taps), taps.shape[1], _lib.i32_array(T), _lib.f32_array(c), _ptr(eta),
+                                          eta.shape[1], _lib.i32_array(kappa), M, _ptr(x2), _ptr(y), n, B,
+                                          _stream()))
+    return y[0] if squeeze else y
+
+
 def ldbp_apply_host_workspace(n, batch) -> int:
     """Device workspace bytes of ldbp_apply_host for [batch, n] waveforms."""
     return int(_lib.lib().ldbp_apply_host_workspace(n, batch))

@@ -83,3 +83,21 @@ def test_ldbp_apply_host_rejects(L, kw, needle):
 def test_ldbp_apply_rejects_nonfinite_coefficient(L, v):
     assert _apply(L, c=[v]) == -6
     assert "NaN or infinite" in L.ldbp_last_error().decode()
+
+
+def _essm(L, kappa=(2,), stride=5, eta=ctypes.c_void_p(64), T=(3,)):
+    M = len(T)
+    return L.ldbp_essm_apply(ctypes.c_void_p(16), 2, _lib.i32_array(list(T)), _lib.f32_array([-0.1] * M), eta, stride,
+                             _lib.i32_array(list(kappa)), M, ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), 128, 1,
+                             None)
+
+
+@pytest.mark.parametrize("kw, needle", [
+    (dict(eta=None), "non-NULL"),
+    (dict(kappa=(25,), stride=51), "kappa[0]=25"),
+    (dict(kappa=(3,), stride=5), "eta_stride"),
+    (dict(T=(19,)), "supported length"),
+])
+def test_ldbp_essm_apply_rejects(L, kw, needle):
+    assert _essm(L, **kw) == -1
+    assert needle in L.ldbp_last_error().decode()
