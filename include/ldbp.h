@@ -207,6 +207,19 @@ int ldbp_backward(const void* taps, int32_t taps_stride, const int32_t* T, const
                   const void* ckpt, const void* gy, void* gx, void* gtaps, int64_t n, int32_t batch, void* workspace,
                   size_t workspace_bytes, void* stream);
 
+/*
+ * ldbp_backward_c -- ldbp_backward that also returns the gradients of the
+ * nonlinear coefficients (the learnable scaling of the nonlinear steps,
+ * Remark 1: c_i = eta_i gamma L_eff(delta_i)):
+ *   dl/dc_i = -sum_{b,m} |v_m|^2 Im(w_m conj(g_w,m)),   v = A_i u_i, w = u_{i+1}.
+ *  gc   device float [M] (output), or NULL (then this is ldbp_backward).
+ * Same workspace, ordering and errors as ldbp_backward; the sums are reduced
+ * in the same fixed order (bitwise reproducible).
+ */
+int ldbp_backward_c(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
+                    const void* ckpt, const void* gy, void* gx, void* gtaps, float* gc, int64_t n, int32_t batch,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
 /* Workspace bytes ldbp_backward needs for (n, batch, T[0..M)).  Host only. */
 int ldbp_backward_workspace(int64_t n, int32_t batch, const int32_t* T, int32_t M, size_t* bytes);
 

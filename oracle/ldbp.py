@@ -24,7 +24,8 @@ that is not available, so this is the unconstrained fit, optionally restricted
 to a band |w| <= w_max.
 
 Pins: dense circulant brute force, adjoint identity <Ax, y> = <x, A^H y>,
-finite-difference gradients, LDBP == asymmetric FD DBP when T = n (n odd).
+finite-difference gradients (taps, input and the coefficients c), LDBP ==
+asymmetric FD DBP when T = n (n odd).
 """
 from __future__ import annotations
 
@@ -88,6 +89,26 @@ def backward(x, taps, c, gy):
         gtaps[i] = gh
         g = fir(gv, np.conj(h))
     return g, gtaps
+
+
+def grad_c(x, taps, c, gy):
+    """Gradients of a real loss with respect to the nonlinear coefficients c_i
+    (the learnable scaling of the nonlinear steps, Remark 1: c_i = eta_i gamma
+    L_eff(delta_i)).  With w = v e^{j c p}, p = |v|^2 and g the gradient at w,
+    dl/dc = Re(conj(g) dw/dc) summed = -sum_m p_m Im(w_m conj(g_m)).
+    Summed over all leading (batch) axes; the reverse sweep is that of backward.
+    """
+    _, inputs = forward(x, taps, c)
+    g = np.asarray(gy, dtype=np.complex128)
+    gc = [0.0] * len(taps)
+    for i in reversed(range(len(taps))):
+        h = np.asarray(taps[i], dtype=np.complex128)
+        v = fir(inputs[i], h)
+        w = kerr(v, c[i])
+        gc[i] = float(-np.sum(np.abs(v) ** 2 * np.imag(w * np.conj(g))))
+        gv = np.exp(-1j * c[i] * np.abs(v) ** 2) * g - 2.0 * c[i] * np.imag(w * np.conj(g)) * v
+        g = fir(gv, np.conj(h))
+    return gc
 
 
 def ls_taps(T: int, xi: float, N: int = 1024, w_max: float = np.pi, gain: float = 1.0):

@@ -47,6 +47,8 @@ _SIGNATURES = {
                         c_void_p, c_float, c_void_p, c_void_p]),
     "ldbp_backward": (c_int, [c_void_p, c_int32, P_int32, P_float, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                               c_int64, c_int32, c_void_p, ctypes.c_size_t, c_void_p]),
+    "ldbp_backward_c": (c_int, [c_void_p, c_int32, P_int32, P_float, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_int64, c_int32, c_void_p, ctypes.c_size_t, c_void_p]),
     "ldbp_backward_static": (c_int, [c_void_p, c_int32, P_int32, P_float, c_int32, c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_int64, c_int32, c_void_p]),
     "ldbp_backward_workspace": (c_int, [c_int64, c_int32, P_int32, c_int32, ctypes.POINTER(ctypes.c_size_t)]),

@@ -213,8 +213,9 @@ def ldbp_backward_workspace_bytes(n, batch, T):
     return out.value
 
 
-def ldbp_backward(taps, T, c, ckpt, gy, want_gx=True, workspace=None, gtaps_out=None):
-    """Adjoint of ldbp_apply: returns (gx or None, gtaps [M, stride]) for the loss gradient gy."""
+def ldbp_backward(taps, T, c, ckpt, gy, want_gx=True, workspace=None, gtaps_out=None, want_gc=False):
+    """Adjoint of ldbp_apply: returns (gx or None, gtaps [M, stride]) for the loss gradient gy,
+    and with want_gc also gc (float32 [M], the gradients of the nonlinear coefficients)."""
     _check_c64("gy", gy)
     _check_c64("taps", taps)
     B, n = gy.shape
@@ -225,10 +226,11 @@ def ldbp_backward(taps, T, c, ckpt, gy, want_gx=True, workspace=None, gtaps_out=
         workspace = torch.empty(max(need, 8), dtype=torch.uint8, device=gy.device)
     gx = torch.empty_like(gy) if want_gx else None
     gt = torch.empty_like(taps) if gtaps_out is None else gtaps_out
-    _lib.check(_lib.lib().ldbp_backward(_ptr(taps), taps.shape[1], _lib.i32_array(T), _lib.f32_array(c), M,
-                                        _ptr(ckpt), _ptr(gy), _ptr(gx), _ptr(gt), n, B, _ptr(workspace),
-                                        workspace.numel(), _stream()))
-    return gx, gt
+    gc = torch.empty(M, dtype=torch.float32, device=gy.device) if want_gc else None
+    _lib.check(_lib.lib().ldbp_backward_c(_ptr(taps), taps.shape[1], _lib.i32_array(T), _lib.f32_array(c), M,
+                                          _ptr(ckpt), _ptr(gy), _ptr(gx), _ptr(gt), _ptr(gc), n, B, _ptr(workspace),
+                                          workspace.numel(), _stream()))
+    return (gx, gt, gc) if want_gc else (gx, gt)
 
 
 class LDBPFunction(torch.autograd.Function):

@@ -167,13 +167,20 @@ int ldbp_backward_workspace(int64_t n, int32_t batch, const int32_t* T, int32_t 
   int kmax = 0;
   if (bwd_plan(n, T, M, &plan, &kmax)) return fail(LDBP_EINVAL, "halo sum too large for one tile");
   const int cls = fwd_kmax_class(kmax);
-  *bytes = (size_t)plan.tiles_per_wave * (size_t)batch * (size_t)M * (size_t)(cls + 1) * sizeof(float2);
+  *bytes = (size_t)plan.tiles_per_wave * (size_t)batch * (size_t)M * (size_t)(cls + 2) * sizeof(float2);
   return LDBP_OK;
 }
 
 int ldbp_backward(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
                   const void* ckpt, const void* gy, void* gx, void* gtaps, int64_t n, int32_t batch, void* workspace,
                   size_t workspace_bytes, void* stream) {
+  return ldbp_backward_c(taps, taps_stride, T, c, M, ckpt, gy, gx, gtaps, nullptr, n, batch, workspace,
+                         workspace_bytes, stream);
+}
+
+int ldbp_backward_c(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
+                    const void* ckpt, const void* gy, void* gx, void* gtaps, float* gc, int64_t n, int32_t batch,
+                    void* workspace, size_t workspace_bytes, void* stream) {
   if (!ckpt || !gy || !gtaps || !workspace)
     return fail(LDBP_EINVAL, "ckpt, gy, gtaps and workspace must be non-NULL");
   if (n < 1 || batch < 1) return fail(LDBP_EINVAL, "n=%lld, batch=%d must be >= 1", (long long)n, batch);
@@ -214,9 +221,13 @@ int ldbp_backward(const void* taps, int32_t taps_stride, const int32_t* T, const
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = launch_ldbp_bwd(p, cls, st);
   if (e != cudaSuccess) return cuda_fail(e, "ldbp_bwd launch");
-  e = launch_tap_reduce(p.partial, plan.tiles_per_wave * batch, M, cls + 1, kk, static_cast<float2*>(gtaps),
+  e = launch_tap_reduce(p.partial, plan.tiles_per_wave * batch, M, cls + 2, kk, static_cast<float2*>(gtaps),
                         taps_stride, st);
   if (e != cudaSuccess) return cuda_fail(e, "tap reduce launch");
+  if (gc) {
+    e = launch_c_reduce(p.partial, plan.tiles_per_wave * batch, M, cls + 2, gc, st);
+    if (e != cudaSuccess) return cuda_fail(e, "c reduce launch");
+  }
   return LDBP_OK;
 }
 

@@ -7,6 +7,8 @@
 //   FIR:   g_u = A_i^H g_v  (the same symmetric filter with conjugated taps)
 //   taps:  dl/dh_0 = sum_m g_v[m] conj(u[m]),
 //          dl/dh_k = sum_m g_v[m] conj(u[m-k] + u[m+k])   (k >= 1).
+//   c:     dl/dc = -sum_m |v_m|^2 Im(w_m conj(g_w,m))  (the learnable scaling of
+//          the nonlinear step, Remark 1).
 // The sweep runs i = M-1 .. 0 inside one kernel.  Each block keeps the
 // gradient of its time tile in registers; u_i is re-read per step from the
 // step-boundary checkpoints written by ldbp_apply (TMA bulk copies,
@@ -27,7 +29,7 @@ struct BwdShared {
   float2* ubuf;    // [2][S]
   float4* taps;    // [M][KMAX+1] (re, re, im, im)
   float2* edges;   // [2 parity][2][NW][kFwdEdge]
-  float2* red;     // [NW][KMAX+1]
+  float2* red;     // [NW][KMAX+2]: tap sums, then the c-gradient sum (.x)
   uint64_t* bars;  // [2]
 };
 
@@ -63,6 +65,7 @@ __device__ __forceinline__ void bwd_step(int i, float2 (&g)[kFwdR], const float2
                  sh.edges + parity * 2 * kFwdNW * kFwdEdge + kFwdNW * kFwdEdge, lane, warp);
   if (K > 0) parity ^= 1;
   float2 gv[kFwdR];
+  float accc = 0.f;  // dl/dc over this thread's own outputs
   if (c != 0.f) {
     float2 v[kFwdR], e[kFwdR];
     tile_fir<K, false>(xe, h, v);
@@ -73,10 +76,17 @@ __device__ __forceinline__ void bwd_step(int i, float2 (&g)[kFwdR], const float2
       const float im = fmaf(w.y, g[r].x, -w.x * g[r].y);  // Im(w conj(g))
       const float2 ge = cmulc(g[r], e[r]);                // g conj(e)
       gv[r] = make_float2(fmaf(-2.f * c * im, v[r].x, ge.x), fmaf(-2.f * c * im, v[r].y, ge.y));
+      if (s0 + r >= 0 && s0 + r < Lt) accc = fmaf(-fmaf(v[r].x, v[r].x, v[r].y * v[r].y), im, accc);
     }
   } else {
+    float2 v[kFwdR];
+    tile_fir<K, false>(xe, h, v);  // w = v when c = 0
 #pragma unroll
-    for (int r = 0; r < kFwdR; ++r) gv[r] = g[r];
+    for (int r = 0; r < kFwdR; ++r) {
+      gv[r] = g[r];
+      const float im = fmaf(v[r].y, g[r].x, -v[r].x * g[r].y);
+      if (s0 + r >= 0 && s0 + r < Lt) accc = fmaf(-fmaf(v[r].x, v[r].x, v[r].y * v[r].y), im, accc);
+    }
   }
   // tap gradients over this block's own output interval
   float2 acc[K + 1];
@@ -98,16 +108,20 @@ __device__ __forceinline__ void bwd_step(int i, float2 (&g)[kFwdR], const float2
       acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, o);
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) accc += __shfl_xor_sync(0xffffffffu, accc, o);
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k <= K; ++k) sh.red[warp * (KMAX + 1) + k] = acc[k];
+    for (int k = 0; k <= K; ++k) sh.red[warp * (KMAX + 2) + k] = acc[k];
+    sh.red[warp * (KMAX + 2) + KMAX + 1] = make_float2(accc, 0.f);
   }
   __syncthreads();
-  if (threadIdx.x <= K) {
+  const int slot = (int)threadIdx.x <= K ? (int)threadIdx.x : (threadIdx.x == KMAX + 1 ? KMAX + 1 : -1);
+  if (slot >= 0) {
     float2 s = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int w = 0; w < kFwdNW; ++w) s = cadd(s, sh.red[w * (KMAX + 1) + threadIdx.x]);
-    p.partial[((long long)blockIdx.x * p.M + i) * (KMAX + 1) + threadIdx.x] = s;
+    for (int w = 0; w < kFwdNW; ++w) s = cadd(s, sh.red[w * (KMAX + 2) + slot]);
+    p.partial[((long long)blockIdx.x * p.M + i) * (KMAX + 2) + slot] = s;
   }
   // g_u = A^H g_v
   float2 ge[kFwdR + 2 * K];
@@ -143,7 +157,7 @@ __global__ void __launch_bounds__(kFwdNT, MINB) ldbp_bwd_kernel(const __grid_con
   sh.taps = reinterpret_cast<float4*>(sh.ubuf + 2 * kFwdS);
   sh.edges = reinterpret_cast<float2*>(sh.taps + p.M * (KMAX + 1));
   sh.red = sh.edges + 4 * kFwdNW * kFwdEdge;
-  sh.bars = reinterpret_cast<uint64_t*>(sh.red + kFwdNW * (KMAX + 1));
+  sh.bars = reinterpret_cast<uint64_t*>(sh.red + kFwdNW * (KMAX + 2));
   __shared__ int timed_out;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -247,8 +261,30 @@ __global__ void __launch_bounds__(256) ldbp_tap_reduce(const float2* __restrict_
   if (threadIdx.x == 0) gtaps[(long long)i * taps_stride + k] = make_float2((float)rx[0], (float)ry[0]);
 }
 
+// gc[i] = sum over blocks (fixed order, FP64) of the c-gradient partials
+// (slot pstride - 1, real part).  One block per step.
+__global__ void __launch_bounds__(256) ldbp_c_reduce(const float2* __restrict__ partial, int tiles, int M, int pstride,
+                                                     float* __restrict__ gc) {
+  const int i = blockIdx.x;
+  double s = 0.0;
+  for (int t = threadIdx.x; t < tiles; t += 256) s += partial[((long long)t * M + i) * pstride + pstride - 1].x;
+  __shared__ double r[256];
+  r[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) r[threadIdx.x] += r[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gc[i] = (float)r[0];
+}
+
+cudaError_t launch_c_reduce(const float2* partial, int tiles, int M, int pstride, float* gc, cudaStream_t st) {
+  ldbp_c_reduce<<<M, 256, 0, st>>>(partial, tiles, M, pstride, gc);
+  return cudaGetLastError();
+}
+
 size_t bwd_smem_bytes(int kmax, int M) {
-  return sizeof(float2) * ((size_t)2 * kFwdS + 4 * kFwdNW * kFwdEdge + (size_t)kFwdNW * (kmax + 1)) +
+  return sizeof(float2) * ((size_t)2 * kFwdS + 4 * kFwdNW * kFwdEdge + (size_t)kFwdNW * (kmax + 2)) +
          sizeof(float4) * (size_t)M * (kmax + 1) + 32;
 }
 

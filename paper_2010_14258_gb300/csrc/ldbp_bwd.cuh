@@ -11,7 +11,7 @@ struct BwdParams {
   const float2* ckpt;    // [M][batch][n]: input of every step
   const float2* gy;      // [batch][n]
   float2* gx;            // [batch][n] or nullptr
-  float2* partial;       // [blocks][M][KMAX+1] per-block tap sums
+  float2* partial;       // [blocks][M][KMAX+2] per-block tap sums, then the c-gradient sum
   const float2* taps;
   int taps_stride;
   long long n;
@@ -31,6 +31,7 @@ struct TapReduceK {
 cudaError_t launch_ldbp_bwd(const BwdParams& p, int kmax_class, cudaStream_t st);
 cudaError_t launch_tap_reduce(const float2* partial, int tiles, int M, int pstride, const TapReduceK& kk,
                               float2* gtaps, int taps_stride, cudaStream_t st);
+cudaError_t launch_c_reduce(const float2* partial, int tiles, int M, int pstride, float* gc, cudaStream_t st);
 size_t bwd_smem_bytes(int kmax, int M);
 
 }  // namespace ldbp

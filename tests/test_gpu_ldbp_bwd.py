@@ -141,3 +141,26 @@ def test_autograd_function():
 def test_training_shape_sampled():
     # 32768-sample waveforms, M = 25, T = 31 (the start of the pruning schedule)
     _check([31] * 25, 3, 32768, 2e-3, seed=77)
+
+
+@pytest.mark.parametrize("Ts,B,n", [([9] * 25, 2, 12000), ([5, 3] * 6 + [1], 2, 9001)])
+def test_backward_c_gradients_match_oracle(Ts, B, n):
+    # Remark 1: gradients of the nonlinear coefficients (learnable scaling);
+    # one linear-only layer (c = 0) still has a c-gradient
+    import torch
+    gpu_lib()
+    from paper_2010_14258_gb300 import api
+    taps, c = _model(Ts, seed=n)
+    c[-1] = 0.0
+    x = _signal(B, n, n + 2, 3e-3)
+    gy = _grad_signal(B, n, n + 3)
+    td, xd = to_dev(_pack(taps)), to_dev(x)
+    ck = torch.empty((len(Ts),) + tuple(xd.shape), dtype=torch.complex64, device="cuda")
+    api.ldbp_apply(td, Ts, c, xd, ckpt=ck)
+    gx, gt, gc = api.ldbp_backward(td, Ts, c, ck, to_dev(gy), want_gc=True)
+    _, gt0 = api.ldbp_backward(td, Ts, c, ck, to_dev(gy))
+    torch.cuda.synchronize()
+    ref = np.array(oldbp.grad_c(x, taps, c, gy))
+    got = gc.cpu().numpy().astype(np.float64)
+    assert rel_l2(got, ref) <= 1e-4
+    assert np.array_equal(to_np(gt), to_np(gt0))  # the tap gradients do not change

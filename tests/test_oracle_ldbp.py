@@ -269,3 +269,28 @@ def test_symmetric_ldbp_layers_equal_symmetric_dbp(log_steps):
     taps = [gi * ldbp.dbp_taps_full(n, -b2 * d * 1e3 * fs ** 2 / 2) for d, gi in zip(dp, g)]
     out, _ = ldbp.forward(y, taps, c)
     assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < 1e-11
+
+
+def test_grad_c_finite_differences():
+    # Remark 1 (learnable scaling of the nonlinear steps): dl/dc_i by central
+    # finite differences of the FP64 forward, for l = sum |y - t|^2 (g = 2 (y - t))
+    rng = np.random.default_rng(12)
+    n, M = 64, 4
+    taps = [synth.complex_normal(3 + 2 * (i % 2), 60 + i, 0.5) for i in range(M)]
+    c = [float(v) for v in rng.uniform(-1.5, 1.5, M)]
+    x = synth.complex_normal(2 * n, 61, 0.8).reshape(2, n)
+    t = synth.complex_normal(2 * n, 62, 0.8).reshape(2, n)
+
+    def loss(cc):
+        y, _ = ldbp.forward(x, taps, cc)
+        return float(np.sum(np.abs(y - t) ** 2))
+
+    y, _ = ldbp.forward(x, taps, c)
+    gc = ldbp.grad_c(x, taps, c, 2.0 * (y - t))
+    for i in range(M):
+        e = 1e-6
+        cp, cm = list(c), list(c)
+        cp[i] += e
+        cm[i] -= e
+        fd = (loss(cp) - loss(cm)) / (2 * e)
+        assert abs(gc[i] - fd) <= 1e-6 * max(1.0, abs(fd)), (i, gc[i], fd)
