@@ -183,3 +183,27 @@ def ldbp_init_symmetric(Ts, n_spans: int, span_km: float, fs: float, steps_per_s
     wm = signal_band(sps, rolloff) * 1.05 if w_max is None else w_max
     taps = [ls_symmetric_fir(T, -b2 * d * 1e3 * fs * fs / 2.0, wm, gain=g) for T, d, g in zip(Ts, dprime, gains)]
     return taps, cs
+
+
+def unit_filters(Ts):
+    """Unit filters h = (1, 0, ..., 0) (Sec. V-E): the link-agnostic initialisation."""
+    out = []
+    for T in Ts:
+        h = np.zeros((T - 1) // 2 + 1, np.complex128)
+        h[0] = 1.0
+        out.append(h)
+    return out
+
+
+def random_filters(Ts, seed: int):
+    """Random filters (Sec. V-E): real and imaginary parts i.i.d. N(0, 1), each filter
+    divided by sum_{k=-K}^{K} |h_k|^2 (the paper's normalisation; its printed bounds
+    -T..T read as -K..K, over both halves of the symmetric filter)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for T in Ts:
+        K = (T - 1) // 2
+        h = rng.normal(size=K + 1) + 1j * rng.normal(size=K + 1)
+        energy = abs(h[0]) ** 2 + 2.0 * float(np.sum(np.abs(h[1:]) ** 2))
+        out.append(h / energy)
+    return out

@@ -9,6 +9,12 @@ symbol indices and powers (seeded), and keeps the pruning schedule: at
 predefined, front-loaded iterations the outermost tap pair of one filter is
 removed (Sec. IV-C, Example 2), choosing the filter whose outermost tap has
 the smallest magnitude among those above their target length.
+
+Options: learnable nonlinear coefficients c_i (the scaling of Remark 1; their
+gradients come from ldbp_backward_c and a host-side Adam updates the M
+values), and the filter initialisations of Sec. V-E: least squares (default),
+unit filters (h = (1, 0, ..., 0), link-agnostic) and random filters
+(i.i.d. N(0, 1) real and imaginary parts, divided by sum_{k=-K}^{K} |h_k|^2).
 """
 from __future__ import annotations
 
@@ -44,6 +50,8 @@ class TrainConfig:
     w_max: float = 0.0             # LS-fit half band (rad/sample); 0: the signal band
     seed: int = 3
     linear_only: bool = False
+    learn_c: bool = False          # train the nonlinear coefficients too (Remark 1)
+    init: str = "ls"               # "ls", "unit" or "random" filters (Sec. V-E)
 
     @property
     def fs(self):
@@ -68,7 +76,15 @@ class Trainer:
         self.T = [cfg.t_start] * M
         taps, c = init.ldbp_init(self.T, span_km=cfg.span_km, fs=cfg.fs, fiber=self.fiber, sps=cfg.sps,
                                  rolloff=cfg.rolloff, w_max=cfg.w_max or None)
+        if cfg.init == "unit":
+            taps = init.unit_filters(self.T)
+        elif cfg.init == "random":
+            taps = init.random_filters(self.T, cfg.seed)
+        elif cfg.init != "ls":
+            raise ValueError(f"unknown initialisation {cfg.init!r}")
         self.c = [0.0] * M if cfg.linear_only else [float(np.float32(ci)) for ci in c]
+        self.mc = np.zeros(M)
+        self.vc = np.zeros(M)
         self.stride = (cfg.t_start - 1) // 2 + 1
         arr = np.zeros((M, self.stride), np.complex64)
         for i, h in enumerate(taps):
@@ -114,15 +130,28 @@ class Trainer:
         need = api.ldbp_backward_workspace_bytes(cfg.n, cfg.batch, self.T)
         if self.ws_bwd is None or self.ws_bwd.numel() < need:
             self.ws_bwd = torch.empty(need, dtype=torch.uint8, device="cuda")
-        _, gt = api.ldbp_backward(self.taps, self.T, self.c, self.ckpt, g, want_gx=False, workspace=self.ws_bwd)
+        res = api.ldbp_backward(self.taps, self.T, self.c, self.ckpt, g, want_gx=False, workspace=self.ws_bwd,
+                                want_gc=cfg.learn_c)
+        gt = res[1]
         self.step_count += 1
         api.adam_step(self.taps, gt, self.m, self.v, self.T, self.step_count, lr=self.lr_at(it))
+        if cfg.learn_c:
+            self.adam_c(res[2].cpu().numpy().astype(np.float64), self.lr_at(it))
         while self.schedule and self.schedule[0] <= it:
             self.schedule.pop(0)
             self.prune_one()
         loss = float(stats[:, 0].mean().item())
         self.history.append(loss)
         return loss
+
+    def adam_c(self, gc, lr, b1=0.9, b2=0.999, eps=1e-8):
+        """Adam on the nonlinear coefficients (host side, M values; same step count as the taps)."""
+        t = self.step_count
+        self.mc = b1 * self.mc + (1 - b1) * gc
+        self.vc = b2 * self.vc + (1 - b2) * gc * gc
+        mh = self.mc / (1 - b1 ** t)
+        vh = self.vc / (1 - b2 ** t)
+        self.c = [float(np.float32(ci - lr * m / (np.sqrt(v) + eps))) for ci, m, v in zip(self.c, mh, vh)]
 
     def lr_at(self, it: int) -> float:
         cfg = self.cfg
@@ -171,7 +200,7 @@ class Trainer:
     def state(self):
         return {"taps": self.taps.cpu().numpy(), "T": np.array(self.T), "c": np.array(self.c),
                 "m": self.m.cpu().numpy(), "v": self.v.cpu().numpy(), "step": self.step_count,
-                "schedule": np.array(self.schedule, dtype=np.int64)}
+                "schedule": np.array(self.schedule, dtype=np.int64), "mc": self.mc, "vc": self.vc}
 
     def save(self, path):
         np.savez(path, **self.state())
@@ -185,3 +214,5 @@ class Trainer:
         self.v.copy_(torch.from_numpy(d["v"]))
         self.step_count = int(d["step"])
         self.schedule = [int(t) for t in d["schedule"]]
+        if "mc" in d:
+            self.mc, self.vc = np.array(d["mc"]), np.array(d["vc"])

@@ -77,3 +77,36 @@ def test_checkpoint_resume_is_bit_identical(tmp_path):
     torch.cuda.synchronize()
     assert a.T == b.T
     assert np.array_equal(a.taps.cpu().numpy(), b.taps.cpu().numpy())
+
+
+def test_learnable_nonlinear_coefficients_train():
+    # Remark 1: with learnable c the coefficients move and training still gains
+    gpu_lib()
+    from paper_2010_14258_gb300.train import Trainer, TrainConfig
+    kw = dict(batch=16, nsym=4096, n_spans=10, channel_steps=20, powers_dbm=(4, 5, 6), t_start=9, t_end=9,
+              iters=600, lr=3e-4, seed=4, learn_c=True)
+    tr = Trainer(TrainConfig(**kw))
+    c0 = list(tr.c)
+    e0 = tr.evaluate(frames=2, power_dbm=5.0)
+    tr.fit()
+    e1 = tr.evaluate(frames=2, power_dbm=5.0)
+    assert max(abs(a - b) / abs(b) for a, b in zip(tr.c, c0)) > 1e-3
+    assert all(np.isfinite(tr.c))
+    assert e1["ldbp"] > e0["ldbp"] + 3.0
+
+
+def test_unit_filter_initialisation_trains():
+    # Sec. V-E: unit filters (no knowledge of the link's dispersion) start with no
+    # CD compensation and converge, more slowly than the LS initialisation
+    gpu_lib()
+    from paper_2010_14258_gb300.train import Trainer, TrainConfig
+    kw = dict(batch=16, nsym=4096, n_spans=10, channel_steps=20, powers_dbm=(4, 5, 6), t_start=9, t_end=9,
+              iters=1500, lr=1e-3, lr_final=1e-4, seed=5, init="unit")
+    tr = Trainer(TrainConfig(**kw))
+    e0 = tr.evaluate(frames=2, power_dbm=5.0)
+    tr.fit()
+    e1 = tr.evaluate(frames=2, power_dbm=5.0)
+    assert e1["ldbp"] > e0["ldbp"] + 10.0
+    rnd = Trainer(TrainConfig(**dict(kw, init="random", iters=50)))
+    rnd.fit()
+    assert np.all(np.isfinite(rnd.taps.cpu().numpy()))
