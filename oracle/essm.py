@@ -39,3 +39,43 @@ def forward(x, taps, c, etas):
         v = ldbp.fir(u, np.asarray(h, dtype=np.complex128))
         u = v * np.exp(1j * ci * filtered_power(v, eta))
     return u, inputs
+
+
+def backward(x, taps, c, etas, gy):
+    """Reverse sweep of the filtered-nonlinearity model.
+
+    Returns (gx, gtaps, getas) for the loss gradient gy (convention
+    g = dl/dRe + j dl/dIm of a real loss), summed over leading (batch) axes.
+    Per step, with v = A u, p = |v|^2, phi = eta * p (circular), w = v e^{j c phi}
+    and g the gradient at w:
+      a_j = dl/dphi_j = -c Im(w_j conj(g_j)),
+      dl/dp_m = sum_k eta_k a_{m+k}          (the filter transposed),
+      g_v = e^{-j c phi} g + 2 (dl/dp) v,
+      dl/deta_k = sum_j a_j p_{j-k},
+    then the FIR adjoint and tap gradients of ldbp.backward.
+    """
+    _, inputs = forward(x, taps, c, etas)
+    g = np.asarray(gy, dtype=np.complex128)
+    gtaps, getas = [None] * len(taps), [None] * len(taps)
+    for i in reversed(range(len(taps))):
+        h = np.asarray(taps[i], dtype=np.complex128)
+        eta = np.asarray(etas[i], dtype=np.float64)
+        kappa = (len(eta) - 1) // 2
+        u = inputs[i]
+        v = ldbp.fir(u, h)
+        p = np.abs(v) ** 2
+        phi = filtered_power(v, eta)
+        w = v * np.exp(1j * c[i] * phi)
+        a = -c[i] * np.imag(w * np.conj(g))
+        dp = np.zeros_like(p)
+        for k in range(-kappa, kappa + 1):
+            dp = dp + eta[k + kappa] * np.roll(a, -k, axis=-1)
+        getas[i] = np.array([np.sum(a * np.roll(p, k, axis=-1)) for k in range(-kappa, kappa + 1)])
+        gv = np.exp(-1j * c[i] * phi) * g + 2.0 * dp * v
+        gh = np.zeros(len(h), dtype=np.complex128)
+        gh[0] = np.sum(gv * np.conj(u))
+        for k in range(1, len(h)):
+            gh[k] = np.sum(gv * np.conj(np.roll(u, k, axis=-1) + np.roll(u, -k, axis=-1)))
+        gtaps[i] = gh
+        g = ldbp.fir(gv, np.conj(h))
+    return g, gtaps, getas
