@@ -106,6 +106,8 @@ int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const fl
  *  eta    device, float [M][eta_stride]: row i holds the real filter
  *         eta^(i)_{-kappa_i} .. eta^(i)_{kappa_i} (2 kappa_i + 1 values).
  *  kappa  host, int32 [M]: 0 <= kappa_i <= LDBP_ESSM_MAX_KAPPA.
+ *  ckpt   device complex64 [M][batch][n] or NULL: receives u_i (the input of
+ *         step i) for ldbp_essm_backward.
  * The tile halo is sum_i (K_i + kappa_i) per side.
  * Errors: LDBP_EINVAL (as ldbp_apply; kappa out of range; eta_stride too
  * small); LDBP_ENONFINITE for a NaN or infinite c_i; LDBP_ECUDA.
@@ -114,7 +116,32 @@ int ldbp_apply(const void* taps, int32_t taps_stride, const int32_t* T, const fl
 #define LDBP_ESSM_MAX_HALF_TAPS 8
 int ldbp_essm_apply(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, const float* eta,
                     int32_t eta_stride, const int32_t* kappa, int32_t M, const void* x, void* y, int64_t n,
-                    int32_t batch, void* stream);
+                    int32_t batch, void* ckpt, void* stream);
+
+/*
+ * ldbp_essm_backward -- adjoint of ldbp_essm_apply.  Given g_y = dl/dRe(y) +
+ * j dl/dIm(y), for i = M-1 .. 0 with v = A_i u_i, p = |v|^2,
+ * phi = eta^(i) * p, w = v exp(j c_i phi) and g the gradient at w:
+ *   a = -c_i Im(w conj(g)),  dl/dp_m = sum_k eta_k a_{m+k},
+ *   g_v = exp(-j c_i phi) g + 2 (dl/dp) v,
+ *   dl/deta^(i)_k = sum_{b,j} a_j p_{j-k},
+ *   taps and g_u = A_i^H g_v as in ldbp_backward.
+ *  ckpt   device complex64 [M][batch][n] from ldbp_essm_apply (ckpt != NULL)
+ *  gtaps  device complex64 [M][taps_stride] (output); entries k > K_i are 0
+ *  geta   device float [M][eta_stride] (output): dl/deta^(i)_k at
+ *         index k + kappa_i; entries beyond 2 kappa_i are 0
+ *  gx     device complex64 [batch][n] (output) or NULL
+ *  workspace  >= ldbp_essm_backward_workspace() bytes, caller-owned
+ * The per-block sums are reduced in a fixed order in FP64 (bitwise
+ * reproducible).  Errors: as ldbp_essm_apply, plus LDBP_EINVAL for a short
+ * workspace or gx aliasing gy / ckpt.
+ */
+int ldbp_essm_backward_workspace(int64_t n, int32_t batch, const int32_t* T, const int32_t* kappa, int32_t M,
+                                 size_t* bytes);
+int ldbp_essm_backward(const void* taps, int32_t taps_stride, const int32_t* T, const float* c, const float* eta,
+                       int32_t eta_stride, const int32_t* kappa, int32_t M, const void* ckpt, const void* gy,
+                       void* gx, void* gtaps, float* geta, int64_t n, int32_t batch, void* workspace,
+                       size_t workspace_bytes, void* stream);
 
 /*
  * ldbp_apply_host -- ldbp_apply on waveforms in HOST memory (the receiver's

@@ -67,7 +67,12 @@ _SIGNATURES = {
                            c_void_p, c_void_p]),
     "ldbp_apply_host_workspace": (ctypes.c_size_t, [c_int64, c_int32]),
     "ldbp_essm_apply": (c_int, [c_void_p, c_int32, P_int32, P_float, c_void_p, c_int32, P_int32, c_int32, c_void_p,
-                                c_void_p, c_int64, c_int32, c_void_p]),
+                                c_void_p, c_int64, c_int32, c_void_p, c_void_p]),
+    "ldbp_essm_backward_workspace": (c_int, [c_int64, c_int32, P_int32, P_int32, c_int32,
+                                             ctypes.POINTER(ctypes.c_size_t)]),
+    "ldbp_essm_backward": (c_int, [c_void_p, c_int32, P_int32, P_float, c_void_p, c_int32, P_int32, c_int32, c_void_p,
+                                   c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, ctypes.c_size_t,
+                                   c_void_p]),
     "ldbp_apply_host": (c_int, [c_void_p, c_int32, P_int32, P_float, c_int32, c_void_p, c_void_p, c_int64, c_int32,
                                 c_int32, c_void_p, ctypes.c_size_t, c_void_p]),
 }

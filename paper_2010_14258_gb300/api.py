@@ -53,10 +53,11 @@ def ldbp_apply(taps, T, c, x, ckpt=None, out=None):
     return y[0] if squeeze else y
 
 
-def ldbp_essm_apply(taps, T, c, eta, kappa, x, out=None):
+def ldbp_essm_apply(taps, T, c, eta, kappa, x, out=None, ckpt=None):
     """Learned enhanced SSM (filtered nonlinear steps, Sec. III-C): ldbp_apply whose
     Kerr phase uses sum_k eta_k |v_{j-k}|^2.  eta: device float32 [M, stride] with
-    row i = (eta_{-kappa_i}, ..., eta_{kappa_i}); kappa: per-step half-widths."""
+    row i = (eta_{-kappa_i}, ..., eta_{kappa_i}); kappa: per-step half-widths;
+    ckpt: optional complex64 [M, B, n] receiving the input of every step."""
     squeeze = x.dim() == 1
     x2 = x.unsqueeze(0) if squeeze else x
     _check_c64("x", x2)
@@ -67,11 +68,35 @@ def ldbp_essm_apply(taps, T, c, eta, kappa, x, out=None):
     M = len(T)
     if taps.shape[0] != M or eta.shape[0] != M or len(kappa) != M:
         raise ValueError("taps, eta and kappa need M = len(T) rows")
+    if ckpt is not None:
+        _check_c64("ckpt", ckpt, (M, B, n))
     y = torch.empty_like(x2) if out is None else out
     _lib.check(_lib.lib().ldbp_essm_apply(_ptr(taps), taps.shape[1], _lib.i32_array(T), _lib.f32_array(c), _ptr(eta),
                                           eta.shape[1], _lib.i32_array(kappa), M, _ptr(x2), _ptr(y), n, B,
-                                          _stream()))
+                                          _ptr(ckpt), _stream()))
     return y[0] if squeeze else y
+
+
+def ldbp_essm_backward(taps, T, c, eta, kappa, ckpt, gy, want_gx=True, workspace=None):
+    """Adjoint of ldbp_essm_apply: returns (gx or None, gtaps [M, stride], geta [M, eta stride])."""
+    import ctypes
+    _check_c64("gy", gy)
+    B, n = gy.shape
+    M = len(T)
+    _check_c64("ckpt", ckpt, (M, B, n))
+    need = ctypes.c_size_t(0)
+    _lib.check(_lib.lib().ldbp_essm_backward_workspace(n, B, _lib.i32_array(T), _lib.i32_array(kappa), M,
+                                                       ctypes.byref(need)))
+    if workspace is None or workspace.numel() < need.value:
+        workspace = torch.empty(max(need.value, 8), dtype=torch.uint8, device=gy.device)
+    gx = torch.empty_like(gy) if want_gx else None
+    gt = torch.empty_like(taps)
+    ge = torch.empty_like(eta)
+    _lib.check(_lib.lib().ldbp_essm_backward(_ptr(taps), taps.shape[1], _lib.i32_array(T), _lib.f32_array(c),
+                                             _ptr(eta), eta.shape[1], _lib.i32_array(kappa), M, _ptr(ckpt), _ptr(gy),
+                                             _ptr(gx), _ptr(gt), _ptr(ge), n, B, _ptr(workspace), workspace.numel(),
+                                             _stream()))
+    return gx, gt, ge
 
 
 def ldbp_apply_host_workspace(n, batch) -> int:

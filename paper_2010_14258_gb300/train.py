@@ -51,6 +51,7 @@ class TrainConfig:
     seed: int = 3
     linear_only: bool = False
     learn_c: bool = False          # train the nonlinear coefficients too (Remark 1)
+    kappa: int = 0                 # > 0: learned enhanced SSM, a (2 kappa + 1)-tap filter on |v|^2 per step
     init: str = "ls"               # "ls", "unit" or "random" filters (Sec. V-E)
 
     @property
@@ -85,6 +86,13 @@ class Trainer:
         self.c = [0.0] * M if cfg.linear_only else [float(np.float32(ci)) for ci in c]
         self.mc = np.zeros(M)
         self.vc = np.zeros(M)
+        if cfg.kappa > 0:  # filters on |v|^2, unit-initialised; stored with an even stride (complex view for Adam)
+            if cfg.learn_c:
+                raise ValueError("learn_c is not supported together with kappa > 0")
+            self.eta = torch.zeros((M, 2 * cfg.kappa + 2), dtype=torch.float32, device="cuda")
+            self.eta[:, cfg.kappa] = 1.0
+            self.me = torch.zeros_like(self.eta)
+            self.ve = torch.zeros_like(self.eta)
         self.stride = (cfg.t_start - 1) // 2 + 1
         arr = np.zeros((M, self.stride), np.complex64)
         for i, h in enumerate(taps):
@@ -125,6 +133,8 @@ class Trainer:
     def train_step(self, it: int) -> float:
         cfg = self.cfg
         sd, pw, y = self.frames(it)
+        if cfg.kappa > 0:
+            return self._train_step_essm(it, sd, pw, y)
         api.ldbp_apply(self.taps, self.T, self.c, y, ckpt=self.ckpt, out=self.out)
         stats, _, g = api.rx(self.out, sd, pw, sps=cfg.sps, rolloff=cfg.rolloff, grad=True, workspace=self.ws_rx)
         need = api.ldbp_backward_workspace_bytes(cfg.n, cfg.batch, self.T)
@@ -143,6 +153,32 @@ class Trainer:
         loss = float(stats[:, 0].mean().item())
         self.history.append(loss)
         return loss
+
+    def _train_step_essm(self, it, sd, pw, y):
+        """One iteration of the learned enhanced SSM: taps and the |v|^2 filters by Adam."""
+        cfg = self.cfg
+        ks = [cfg.kappa] * self.M
+        api.ldbp_essm_apply(self.taps, self.T, self.c, self.eta, ks, y, ckpt=self.ckpt, out=self.out)
+        stats, _, g = api.rx(self.out, sd, pw, sps=cfg.sps, rolloff=cfg.rolloff, grad=True, workspace=self.ws_rx)
+        _, gt, ge = api.ldbp_essm_backward(self.taps, self.T, self.c, self.eta, ks, self.ckpt, g, want_gx=False)
+        self.step_count += 1
+        lr = self.lr_at(it)
+        api.adam_step(self.taps, gt, self.m, self.v, self.T, self.step_count, lr=lr)
+        api.adam_step(torch.view_as_complex(self.eta.view(self.M, -1, 2)), torch.view_as_complex(ge.view(self.M, -1, 2)),
+                      self.me.view(self.M, -1, 2), self.ve.view(self.M, -1, 2), [2 * cfg.kappa + 1] * self.M,
+                      self.step_count, lr=lr)
+        while self.schedule and self.schedule[0] <= it:
+            self.schedule.pop(0)
+            self.prune_one()
+        loss = float(stats[:, 0].mean().item())
+        self.history.append(loss)
+        return loss
+
+    def apply(self, y):
+        """The trained model on received waveforms y (device complex64 [B, n])."""
+        if self.cfg.kappa > 0:
+            return api.ldbp_essm_apply(self.taps, self.T, self.c, self.eta, [self.cfg.kappa] * self.M, y)
+        return api.ldbp_apply(self.taps, self.T, self.c, y)
 
     def adam_c(self, gc, lr, b1=0.9, b2=0.999, eps=1e-8):
         """Adam on the nonlinear coefficients (host side, M values; same step count as the taps)."""
@@ -186,7 +222,7 @@ class Trainer:
         acc = {"ldbp": [0.0, 0.0], "dbp": [0.0, 0.0]}
         for f in range(frames):
             sd, pw, y = self.frames(first_frame + f, powers_dbm=(power_dbm,))
-            out = api.ldbp_apply(self.taps, self.T, self.c, y)
+            out = self.apply(y)
             st, _, _ = api.rx(out, sd, pw, sps=cfg.sps, rolloff=cfg.rolloff)
             z = api.dbp_apply(self.fiber, self.link(0), cfg.fs, y, steps_per_span=1, symmetric=False)
             sd2, _, _ = api.rx(z, sd, pw, sps=cfg.sps, rolloff=cfg.rolloff)
@@ -200,7 +236,9 @@ class Trainer:
     def state(self):
         return {"taps": self.taps.cpu().numpy(), "T": np.array(self.T), "c": np.array(self.c),
                 "m": self.m.cpu().numpy(), "v": self.v.cpu().numpy(), "step": self.step_count,
-                "schedule": np.array(self.schedule, dtype=np.int64), "mc": self.mc, "vc": self.vc}
+                "schedule": np.array(self.schedule, dtype=np.int64), "mc": self.mc, "vc": self.vc,
+                **({"eta": self.eta.cpu().numpy(), "me": self.me.cpu().numpy(), "ve": self.ve.cpu().numpy()}
+                   if self.cfg.kappa > 0 else {})}
 
     def save(self, path):
         np.savez(path, **self.state())
@@ -216,3 +254,6 @@ class Trainer:
         self.schedule = [int(t) for t in d["schedule"]]
         if "mc" in d:
             self.mc, self.vc = np.array(d["mc"]), np.array(d["vc"])
+        if self.cfg.kappa > 0:
+            for name in ("eta", "me", "ve"):
+                getattr(self, name).copy_(torch.from_numpy(d[name]))

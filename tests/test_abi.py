@@ -89,7 +89,7 @@ def _essm(L, kappa=(2,), stride=5, eta=ctypes.c_void_p(64), T=(3,)):
     M = len(T)
     return L.ldbp_essm_apply(ctypes.c_void_p(16), 2, _lib.i32_array(list(T)), _lib.f32_array([-0.1] * M), eta, stride,
                              _lib.i32_array(list(kappa)), M, ctypes.c_void_p(4096), ctypes.c_void_p(1 << 20), 128, 1,
-                             None)
+                             None, None)
 
 
 @pytest.mark.parametrize("kw, needle", [

@@ -71,3 +71,43 @@ def test_unit_filter_matches_ldbp_apply():
     y = _run(taps, Ts, c, [np.array([1.0])] * 10, [0] * 10, x)
     y0 = to_np(api.ldbp_apply(to_dev(_pack(taps)), Ts, c, to_dev(x)))
     assert rel_l2(y, y0) <= 1e-6
+
+
+def _eta_dev(etas):
+    import torch
+    stride = max(len(e) for e in etas)
+    ed = np.zeros((len(etas), stride), np.float32)
+    for i, e in enumerate(etas):
+        ed[i, : len(e)] = e
+    return torch.from_numpy(ed).cuda()
+
+
+@pytest.mark.parametrize("Ts,kappas,B,n", [
+    ([9] * 8, [6] * 8, 2, 9000),
+    ([5, 3, 1, 7], [20, 0, 3, 8], 1, 8192),
+    ([3, 3], [2, 1], 2, 1001),
+])
+def test_essm_backward_parity(Ts, kappas, B, n):
+    import torch
+    from paper_2010_14258_gb300 import api
+    from tests.test_gpu_ldbp_bwd import _grad_signal
+    gpu_lib()
+    taps, c = _model(Ts, seed=n + 1)
+    etas = _etas(kappas, n + 2)
+    x = _signal(B, n, n + 3, 3e-3)
+    gy = _grad_signal(B, n, n + 4)
+    td, xd, ed = to_dev(_pack(taps)), to_dev(x), _eta_dev(etas)
+    ck = torch.empty((len(Ts),) + tuple(xd.shape), dtype=torch.complex64, device="cuda")
+    y = api.ldbp_essm_apply(td, Ts, c, ed, kappas, xd, ckpt=ck)
+    gx, gt, ge = api.ldbp_essm_backward(td, Ts, c, ed, kappas, ck, to_dev(gy))
+    torch.cuda.synchronize()
+    rgx, rgt, rge = essm.backward(x, taps, c, etas, gy)
+    assert rel_l2(to_np(gx), rgx) <= 1e-4
+    for i in range(len(Ts)):
+        h = rgt[i]
+        assert rel_l2(to_np(gt)[i, : len(h)], h) <= 1e-4, i
+        e = rge[i]
+        assert rel_l2(ge.cpu().numpy()[i, : len(e)].astype(np.float64), e) <= 1e-4, i
+        assert np.all(ge.cpu().numpy()[i, len(e):] == 0)
+    _, inputs = essm.forward(x, taps, c, etas)
+    assert rel_l2(to_np(ck[-1]), inputs[-1]) <= 1e-4

@@ -110,3 +110,19 @@ def test_unit_filter_initialisation_trains():
     rnd = Trainer(TrainConfig(**dict(kw, init="random", iters=50)))
     rnd.fit()
     assert np.all(np.isfinite(rnd.taps.cpu().numpy()))
+
+
+def test_learned_essm_trains():
+    # learned enhanced SSM (Sec. III-C): FIR taps and per-step |v|^2 filters
+    # (unit-initialised) trained jointly by Adam through ldbp_essm_backward
+    gpu_lib()
+    from paper_2010_14258_gb300.train import Trainer, TrainConfig
+    kw = dict(batch=16, nsym=4096, n_spans=10, channel_steps=20, powers_dbm=(4, 5, 6), t_start=9, t_end=9,
+              iters=600, lr=3e-4, seed=6, kappa=8)
+    tr = Trainer(TrainConfig(**kw))
+    eta0 = tr.eta.clone()
+    e0 = tr.evaluate(frames=2, power_dbm=5.0)
+    tr.fit()
+    e1 = tr.evaluate(frames=2, power_dbm=5.0)
+    assert float((tr.eta - eta0).abs().max()) > 1e-3
+    assert e1["ldbp"] > e0["ldbp"] + 3.0
