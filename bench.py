@@ -55,6 +55,11 @@ SMS, FP32_LANES, SM_MAX_HZ = 152, 128, 2.07e9
 FP32_PEAK_FLOPS = 2 * SMS * FP32_LANES * SM_MAX_HZ
 
 
+# plain FD DBP: two n-point FFTs (5 n log2 n flops each), the spectral multiply
+# (6) and the Kerr step (10) per sample and step
+DBP_FLOPS_PER_SAMPLE_STEP = 2 * 5 * int(np.log2(N_SAMP)) + 6 + 10
+
+
 def ldbp_flops_per_sample_step(T: int) -> int:
     """Algorithmic FP32 work of one LDBP step per complex sample (direct form).
 
@@ -630,6 +635,8 @@ def main():
            "snr": {"ldbp_db": snrs[T_head], "dbp_1stps_db": snr_dbp, "delta_db": snrs[T_head] - snr_dbp,
                    "gate_met": T_head in ok, "all_trained": {str(k): v for k, v in snrs.items()}},
            "dbp": {"fused_samples_steps_per_s": units / (dbp_ms / 1e3), "fused_ms": dbp_ms,
+                   "fused_frac_fp32": DBP_FLOPS_PER_SAMPLE_STEP * units / (dbp_ms / 1e3) / FP32_PEAK_FLOPS,
+                   "fused_work": "2*5*log2(n) + 6 + 10 flops per sample-step (two FFTs, spectral multiply, Kerr)",
                    "cufft_samples_steps_per_s": units / (cufft_ms / 1e3), "cufft_ms": cufft_ms,
                    "ldbp_speedup_vs_fused_dbp": dbp_ms / (ms / args.steps),
                    "ldbp_speedup_vs_cufft_dbp": cufft_ms / (ms / args.steps)},
