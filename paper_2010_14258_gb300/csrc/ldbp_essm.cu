@@ -22,6 +22,10 @@ namespace ldbp {
 namespace {
 
 constexpr int kER = 16, kENT = 256, kENW = kENT / 32, kES = kER * kENT;
+// Power buffers are padded by 4 floats per 16: a thread's 16 values start at
+// 20 t floats, so 16-byte accesses of 8 consecutive threads hit distinct banks.
+constexpr int kEPad = kES + kES / 4;
+__device__ __forceinline__ int ppad(int j) { return j + ((j >> 4) << 2); }
 
 struct EssmParams {
   const float2* x;
@@ -70,7 +74,7 @@ __device__ __forceinline__ void essm_kerr(float2 (&v)[kER], const float* __restr
                                           int tid) {
   constexpr int W = kER + 2 * KAPPA;
   {
-    float4* p4 = reinterpret_cast<float4*>(pbuf + tid * kER);
+    float4* p4 = reinterpret_cast<float4*>(pbuf + ppad(tid * kER));
 #pragma unroll
     for (int r = 0; r < kER; r += 4)
       p4[r / 4] = make_float4(fmaf(v[r].x, v[r].x, v[r].y * v[r].y), fmaf(v[r + 1].x, v[r + 1].x, v[r + 1].y * v[r + 1].y),
@@ -82,10 +86,9 @@ __device__ __forceinline__ void essm_kerr(float2 (&v)[kER], const float* __restr
   float pw[W];
   const int s0 = tid * kER - KAPPA;
   if (s0 >= 0 && s0 + W <= kES && (KAPPA % 4) == 0) {
-    const float4* q4 = reinterpret_cast<const float4*>(pbuf + s0);
 #pragma unroll
     for (int j = 0; j < W / 4; ++j) {
-      const float4 q = q4[j];
+      const float4 q = *reinterpret_cast<const float4*>(pbuf + ppad(s0 + 4 * j));
       pw[4 * j] = q.x;
       pw[4 * j + 1] = q.y;
       pw[4 * j + 2] = q.z;
@@ -93,7 +96,7 @@ __device__ __forceinline__ void essm_kerr(float2 (&v)[kER], const float* __restr
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < W; ++j) pw[j] = (s0 + j >= 0 && s0 + j < kES) ? pbuf[s0 + j] : 0.f;
+    for (int j = 0; j < W; ++j) pw[j] = (s0 + j >= 0 && s0 + j < kES) ? pbuf[ppad(s0 + j)] : 0.f;
   }
   float q[kER];
 #pragma unroll
@@ -136,8 +139,8 @@ template <int KMAX, int KAPPA>
 __global__ void __launch_bounds__(kENT, 2) ldbp_essm_kernel(const __grid_constant__ EssmParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2* tile = reinterpret_cast<float2*>(smem_raw);
-  float* pbufs = reinterpret_cast<float*>(tile + kES);                     // [2][kES]
-  float4* taps_s = reinterpret_cast<float4*>(pbufs + 2 * kES);             // [M][KMAX+1]
+  float* pbufs = reinterpret_cast<float*>(tile + kES);                     // [2][kEPad]
+  float4* taps_s = reinterpret_cast<float4*>(pbufs + 2 * kEPad);           // [M][KMAX+1]
   float* eta_s = reinterpret_cast<float*>(taps_s + p.M * (KMAX + 1));      // [M][2 KAPPA + 1], zero-padded
   float2* edges = reinterpret_cast<float2*>(eta_s + ((p.M * (2 * KAPPA + 1) + 3) & ~3));  // [2][2][NW][edge]
   uint64_t* bar = reinterpret_cast<uint64_t*>(edges + 4 * kENW * kFwdEdge);
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(kENT, 2) ldbp_essm_kernel(const __grid_constan
     float2* ef = edges + parity * 2 * kENW * kFwdEdge;
     float2* el = ef + kENW * kFwdEdge;
     essm_dispatch<KMAX, KAPPA>(p.K[i], v, taps_s + i * (KMAX + 1), eta_s + i * EW, p.c[i], ef, el,
-                               pbufs + (i & 1) * kES, lane, warp, tid);
+                               pbufs + (i & 1) * kEPad, lane, warp, tid);
     if (p.K[i] > 0) parity ^= 1;
   }
 
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(kENT, 2) ldbp_essm_kernel(const __grid_constan
 }
 
 size_t essm_smem_bytes(int kmax, int kappa, int M) {
-  return sizeof(float2) * (size_t)kES + sizeof(float) * 2 * (size_t)kES + sizeof(float4) * (size_t)M * (kmax + 1) +
+  return sizeof(float2) * (size_t)kES + sizeof(float) * 2 * (size_t)kEPad + sizeof(float4) * (size_t)M * (kmax + 1) +
          sizeof(float) * (size_t)((M * (2 * kappa + 1) + 3) & ~3) + sizeof(float2) * 4 * kENW * kFwdEdge + 16;
 }
 
@@ -305,10 +308,9 @@ __device__ __forceinline__ void expj_by_power(const float (&q)[kER], float c, fl
 template <int W>
 __device__ __forceinline__ void read_window(const float* buf, int s0, float (&out)[W]) {
   if (s0 >= 0 && s0 + W <= kES && (s0 & 3) == 0 && (W & 3) == 0) {
-    const float4* q4 = reinterpret_cast<const float4*>(buf + s0);
 #pragma unroll
     for (int j = 0; j < W / 4; ++j) {
-      const float4 q = q4[j];
+      const float4 q = *reinterpret_cast<const float4*>(buf + ppad(s0 + 4 * j));
       out[4 * j] = q.x;
       out[4 * j + 1] = q.y;
       out[4 * j + 2] = q.z;
@@ -316,20 +318,20 @@ __device__ __forceinline__ void read_window(const float* buf, int s0, float (&ou
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < W; ++j) out[j] = (s0 + j >= 0 && s0 + j < kES) ? buf[s0 + j] : 0.f;
+    for (int j = 0; j < W; ++j) out[j] = (s0 + j >= 0 && s0 + j < kES) ? buf[ppad(s0 + j)] : 0.f;
   }
 }
 
 __device__ __forceinline__ void write_tile16(float* buf, int tid, const float (&a)[kER]) {
-  float4* p4 = reinterpret_cast<float4*>(buf + tid * kER);
+  float4* p4 = reinterpret_cast<float4*>(buf + ppad(tid * kER));
 #pragma unroll
   for (int r = 0; r < kER; r += 4) p4[r / 4] = make_float4(a[r], a[r + 1], a[r + 2], a[r + 3]);
 }
 
 struct EssmBwdShared {
   float2* ubuf;   // [2][kES]
-  float* pbuf;    // [kES]
-  float* abuf;    // [kES]
+  float* pbuf;    // [kEPad]
+  float* abuf;    // [kEPad]
   float4* taps;   // [M][KMAX+1]
   float* eta;     // [M][2 KAPPA + 1], zero-padded
   float2* edges;  // [2][2][NW][edge]
@@ -495,8 +497,8 @@ __global__ void __launch_bounds__(kENT, 1) ldbp_essm_bwd_kernel(const __grid_con
   EssmBwdShared sh;
   sh.ubuf = reinterpret_cast<float2*>(smem_raw);
   sh.pbuf = reinterpret_cast<float*>(sh.ubuf + 2 * kES);
-  sh.abuf = sh.pbuf + kES;
-  sh.taps = reinterpret_cast<float4*>(sh.abuf + kES);
+  sh.abuf = sh.pbuf + kEPad;
+  sh.taps = reinterpret_cast<float4*>(sh.abuf + kEPad);
   sh.eta = reinterpret_cast<float*>(sh.taps + p.M * (KMAX + 1));
   sh.edges = reinterpret_cast<float2*>(sh.eta + ((p.M * EW + 3) & ~3));
   sh.red = sh.edges + 4 * kENW * kFwdEdge;
@@ -621,7 +623,7 @@ __global__ void __launch_bounds__(256) essm_reduce(const float2* __restrict__ pa
 
 size_t essm_bwd_smem_bytes(int kmax, int kappa, int M) {
   const int ew = 2 * kappa + 1, pst = kmax + 1 + ew;
-  return sizeof(float2) * 2 * (size_t)kES + sizeof(float) * 2 * (size_t)kES + sizeof(float4) * (size_t)M * (kmax + 1) +
+  return sizeof(float2) * 2 * (size_t)kES + sizeof(float) * 2 * (size_t)kEPad + sizeof(float4) * (size_t)M * (kmax + 1) +
          sizeof(float) * (size_t)((M * ew + 3) & ~3) + sizeof(float2) * (4 * kENW * kFwdEdge + (size_t)kENW * pst) + 32;
 }
 
