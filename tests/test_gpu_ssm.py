@@ -129,3 +129,31 @@ def test_full_size_dbp_sampled():
     for b in (0, 131, 255):
         ref = nlse.dbp(to_np(x[b]), fib, link, fs, steps_per_span=1, symmetric=False)
         assert rel_l2(to_np(y[b]), ref) <= 1e-4
+
+
+@pytest.mark.parametrize("B,n,fs,spans,span_km,stps,sps", [
+    (64, 32768, 20e9, 25, 80.0, 100, 2),    # the training channel: 25 x 80 km, 100 StPS, ASE
+    (128, 131072, 128e9, 10, 100.0, 200, 4),  # 32 GBd at 4 samples/symbol, 10 x 100 km, 200 StPS, ASE
+])
+def test_full_size_channel_sampled(B, n, fs, spans, span_km, stps, sps):
+    # full-size channel runs with ASE: a sampled waveform vs the oracle (same
+    # Philox noise).  The FP32 error of a split-step run grows linearly with
+    # the step count (the rounded twiddles and spectral tables act the same
+    # way every step): allow 4e-7 per step (about 3 FP32 ulps), and require the
+    # fused kernel to be within 2x of the cuFFT evaluation of the same program.
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    fib = synth.Fiber()
+    link = synth.Link(spans, span_km, stps, True, True, 5.0, 1.946e14, seed=123, counter=7)
+    x = _sig(B, n, 17, 1.585e-3, sps=sps)
+    xd = to_dev(x)
+    y = api.ssm_forward(fib, link, fs, xd)
+    yc = api.ssm_cufft(fib, link, fs, xd[0:1].contiguous())
+    torch.cuda.synchronize()
+    steps = spans * stps
+    # waveform 0 (its ASE draws use waveform index 0, as in a one-waveform oracle run)
+    ref = nlse.channel(x[0:1], fib, link, fs)
+    err, err_cufft = rel_l2(to_np(y[0:1]), ref), rel_l2(to_np(yc), ref)
+    assert err <= 4e-7 * steps
+    assert err <= 2.0 * err_cufft + 1e-6
