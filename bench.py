@@ -202,6 +202,19 @@ def traffic_from_profiles(kernel: str, T: int):
     return rec.get("bytes_per_launch")
 
 
+def job_throughput(ms_local: float, units_per_rank: int, steps: int, world: int, device: str = "cpu"):
+    """Whole-job throughput of a weak-scaling replica run: the slowest rank's
+    time (max over ranks) and the units of all ranks per second."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank * steps / (ms / 1e3)
+
+
 def cpu_baseline_ldbp(T: int, seconds: float = 10.0, max_waves: int = 64):
     """The FP64 oracle (numpy, one host core) on a bounded sample of the workload."""
     from oracle import ldbp as oldbp
@@ -592,13 +605,9 @@ def main():
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     clocks = cs_.summary()
     units = B * N_SAMP * M_STEPS
-    value = world * units * args.steps / (ms / 1e3)
+    ms, value = job_throughput(ms, units, args.steps, world, device="cuda")
     per_launch_s = ms / 1e3 / args.steps
     flops = sum(ldbp_flops_per_sample_step(T) for T in Ts) * B * N_SAMP
     achieved = flops / per_launch_s / 1e12
