@@ -73,7 +73,8 @@ __device__ __forceinline__ void tile_fir(const float2 (&xe)[R + 2 * K], const fl
       A = __ffma2_rn(hr[k], sk, A);
       Bv = __ffma2_rn(hi[k], sk, Bv);
     }
-    out[r] = CONJ ? make_float2(A.x + Bv.y, A.y - Bv.x) : make_float2(A.x - Bv.y, A.y + Bv.x);
+    // (A.re - Bv.im, A.im + Bv.re) as one packed FMA on the swapped Bv (exact: a single rounding per part)
+    out[r] = __ffma2_rn(make_float2(Bv.y, Bv.x), CONJ ? make_float2(1.f, -1.f) : make_float2(-1.f, 1.f), A);
   }
 }
 
