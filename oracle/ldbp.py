@@ -13,7 +13,9 @@ Adjoint (gradients in the convention g = dl/dRe + j dl/dIm of a real loss):
   Kerr y = x e^{j c |x|^2}:  gx = e^{-j c |x|^2} gy - 2 c Im(y conj(gy)) x
   FIR  y = A x:               gx = A^H gy  (the same symmetric FIR with conj taps)
   taps:  dl/dh_0 = sum_m gv_m conj(x_m);  dl/dh_k = sum_m gv_m conj(x_{m-k} + x_{m+k})
-The Kerr adjoint is derived with Wirtinger calculus (see DESIGN); it is pinned by
+The Kerr adjoint follows from Wirtinger calculus: with E = e^{j c |x|^2},
+dy = E (1 + j c |x|^2) dx + j c E x^2 dx*, so 2 dl/dx* = conj(E)(1 - j c |x|^2) g +
+j c E x^2 conj(g) = conj(E) g - 2 c Im(y conj(g)) x; it is pinned by
 central finite differences on the FP64 forward (tests/test_oracle_ldbp.py).
 
 Least-squares initialisation (Sec. IV-C): minimise ||B h - d||^2 with
