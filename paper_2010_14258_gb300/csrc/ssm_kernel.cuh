@@ -50,8 +50,18 @@ __host__ __device__ constexpr int ssm_stage_offset(int logn2, int logns_target) 
 
 // One radix-R Stockham pass of the local N2-point forward FFT (in place,
 // loads complete before stores).  Ns = product of the earlier radices.
-template <int LOGN2, int LOGNS, int LOGR, bool LAST_OF_INVERSE>
-__device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict__ stw, float c) {
+// PUSH_P > 1 (last pass of the forward transform in a P-block cluster): the
+// outputs go straight to their owners' receive buffers (st.async counted on
+// the owner's bars[0]) instead of local shared memory: output k2 belongs to
+// block k2 / C at position r C + k2 % C, C = N2 / P.
+struct SsmPush {
+  uint32_t recv_l, bar0_l;
+  int r;
+};
+
+template <int LOGN2, int LOGNS, int LOGR, bool LAST_OF_INVERSE, int PUSH_P = 0>
+__device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict__ stw, float c,
+                                         const SsmPush& push = SsmPush{0u, 0u, 0}) {
   constexpr int N2 = 1 << LOGN2, R = 1 << LOGR, Ns = 1 << LOGNS, NT = N2 / kSsmE, NB = kSsmE / R;
   const float2* __restrict__ tw = stw + ssm_stage_offset(LOGN2, LOGNS);
   const int t = threadIdx.x;
@@ -81,18 +91,30 @@ __device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict_
       if (c != 0.f) tile_kerr<kSsmE>(a, c);
     }
     const int base = (j - k) * R + k;
+    if constexpr (PUSH_P > 1) {
+      constexpr int C = N2 / PUSH_P;
 #pragma unroll
-    for (int q = 0; q < R; ++q) sbuf[spad(base + q * Ns)] = a[i * R + q];
+      for (int q = 0; q < R; ++q) {
+        const int k2 = base + q * Ns, owner = k2 / C;
+        st_async_c64(mapa_shared(push.recv_l + (uint32_t)(push.r * C + k2 - owner * C) * sizeof(float2), owner),
+                     a[i * R + q], mapa_shared(push.bar0_l, owner));
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) sbuf[spad(base + q * Ns)] = a[i * R + q];
+    }
   }
   __syncthreads();
 }
 
-template <int LOGN2, int LOGNS, bool INVERSE>
-__device__ __forceinline__ void ssm_local_fft(float2* sbuf, const float2* stw, float c) {
+template <int LOGN2, int LOGNS, bool INVERSE, int PUSH_P = 0>
+__device__ __forceinline__ void ssm_local_fft(float2* sbuf, const float2* stw, float c,
+                                              const SsmPush& push = SsmPush{0u, 0u, 0}) {
   if constexpr (LOGNS < LOGN2) {
     constexpr int LOGR = (LOGNS == 0 && (LOGN2 % 4) != 0) ? (LOGN2 % 4) : 4;
-    ssm_pass<LOGN2, LOGNS, LOGR, INVERSE && (LOGNS + LOGR == LOGN2)>(sbuf, stw, c);
-    ssm_local_fft<LOGN2, LOGNS + LOGR, INVERSE>(sbuf, stw, c);
+    constexpr bool last = LOGNS + LOGR == LOGN2;
+    ssm_pass<LOGN2, LOGNS, LOGR, INVERSE && last, (!INVERSE && last) ? PUSH_P : 0>(sbuf, stw, c, push);
+    ssm_local_fft<LOGN2, LOGNS + LOGR, INVERSE, PUSH_P>(sbuf, stw, c, push);
   }
 }
 
@@ -132,17 +154,12 @@ __device__ __forceinline__ bool ssm_middle(float2* sbuf, float2* recv, uint64_t*
     for (int q = 1; q < P; ++q) wv[i][q - 1] = __ldg(&p.twiddle[(q - 1) * N2 + k2]);
   }
   if constexpr (P > 1) {
+    // the forward transform's last pass has pushed this block's spectrum to the
+    // owners (possibly before this expect_tx: the phase cannot complete before
+    // this arrival, and the transaction count may go transiently negative)
     if (t == 0) {
       mbar_arrive_expect_tx(&bars[0], N2 * sizeof(float2));
       mbar_arrive_expect_tx(&bars[1], N2 * sizeof(float2));
-    }
-    const uint32_t recv_l = smem_u32(recv) + (uint32_t)(r * C) * sizeof(float2), bar0_l = smem_u32(&bars[0]);
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-      const uint32_t dst = mapa_shared(recv_l, q), rbar = mapa_shared(bar0_l, q);
-#pragma unroll
-      for (int i = 0; i < NK; ++i)
-        st_async_c64(dst + (uint32_t)(t + i * NT) * sizeof(float2), sbuf[spad(q * C + t + i * NT)], rbar);
     }
     ok = mbar_wait_cluster_bounded(&bars[0], phase, 1 << 20);
   }
@@ -226,9 +243,10 @@ __global__ void __launch_bounds__((1 << LOGN2) / kSsmE, (512 / ((1 << LOGN2) / k
     fence_mbar_init();
   }
   cluster_barrier<P>(cl);  // every block of the cluster is running (barriers initialised) before remote access
+  const SsmPush push{smem_u32(recv), smem_u32(&bars[0]), r};
   for (int s = 0; s < p.nsteps; ++s) {
     const SsmStep st = p.steps[s];
-    ssm_local_fft<LOGN2, 0, false>(sbuf, stw, 0.f);
+    ssm_local_fft<LOGN2, 0, false, P>(sbuf, stw, 0.f, push);
     if (!ssm_middle<LOGN2, P>(sbuf, recv, bars, (uint32_t)(s & 1), r, b, st, p, s == 0)) stop = 1;
     ssm_local_fft<LOGN2, 0, true>(sbuf, stw, st.c);  // its barriers make `stop` visible
     if (stop) break;
