@@ -4,15 +4,19 @@
 // as linear step and the Kerr rotation x exp(j c |x|^2) as nonlinear step.
 //
 // Design (GB300):
-//  * One thread block = 256 threads x 16 consecutive samples = a 4096-sample
-//    tile that covers an output interval of L samples plus the summed
-//    overlap-save halo Hp >= sum_i K_i on each side (circular wrap at the
-//    waveform ends).  The tile is read from HBM once with a TMA bulk copy
-//    (cp.async.bulk, completion on an mbarrier) and written back once with a
-//    bulk store: 16 bytes of HBM traffic per sample for all M steps.
+//  * One thread block holds a 4096-sample tile: 128 threads x 32 consecutive
+//    samples (fixed-width instances and the per-step dispatch up to K = 8) or
+//    256 threads x 16 samples (the dispatch for K <= 2 and K <= 16).  The
+//    tile covers an output interval of L samples plus the summed overlap-save
+//    halo Hp >= sum_i K_i on each side (circular wrap at the waveform ends).
+//    It is read from HBM once with a TMA bulk copy (cp.async.bulk, completion
+//    on an mbarrier) and written back once with a bulk store: 16 bytes of HBM
+//    traffic per sample for all M steps.
 //  * The samples live in registers for all M steps.  Neighbour samples for
 //    the FIR come from the adjacent lanes by warp shuffles; only the two
 //    edge lanes of every warp exchange K samples through shared memory.
+//  * The Kerr step evaluates exp(j c |v|^2) with the minimax polynomial tiers
+//    of ldbp_tile.cuh (FP32x2 packed, no special-function unit).
 //  * The FIR uses the folded form of Fig. 3: y_m = h_0 x_m + sum_k h_k (x_{m-k} + x_{m+k}).
 //  * The valid window shrinks by K_i per side per step; after M steps the
 //    interior [Hp, Hp + L) of the tile is exact.

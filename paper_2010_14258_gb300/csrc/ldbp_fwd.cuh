@@ -8,6 +8,9 @@
 
 namespace ldbp {
 
+// Default register-tile geometry (the adjoint, the filtered-power kernels and
+// the forward instances with K <= 2 or K <= 16 dispatch); the other forward
+// and ragged instances use 32 samples per thread in 128-thread blocks.
 constexpr int kFwdR = 16;                 // consecutive samples held by one thread
 constexpr int kFwdNT = 256;               // threads per block
 constexpr int kFwdNW = kFwdNT / 32;       // warps per block

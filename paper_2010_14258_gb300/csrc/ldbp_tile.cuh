@@ -1,6 +1,7 @@
 // Register-tile helpers shared by the fused learned-DBP kernels: each thread
-// holds kFwdR consecutive samples; neighbours come from adjacent lanes by warp
-// shuffles and from adjacent warps through a small shared-memory edge buffer.
+// holds R consecutive samples (a template parameter, default kFwdR); neighbours
+// come from adjacent lanes by warp shuffles and from adjacent warps through a
+// small shared-memory edge buffer.
 #pragma once
 
 #include "common.cuh"
