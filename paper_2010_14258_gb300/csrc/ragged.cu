@@ -4,8 +4,9 @@
 // through the same fused tile computation as ldbp_apply (Eq. (7) with the
 // FIR of Sec. III-B).  The host builds a work list of (waveform, tile) items
 // sorted by decreasing cost (longest-processing-time first); a persistent
-// grid of one or two blocks per SM takes items from a device counter until
-// the list is exhausted (no spinning: one atomic fetch per item).  The tile
+// grid (autotuned blocks per SM, up to the occupancy of the K_max class)
+// takes items from a device counter until the list is exhausted (no
+// spinning: one atomic fetch per item).  The tile
 // length per waveform is capped by an autotuned limit that trades halo
 // overhead against load balance; the plan can be captured once into a CUDA
 // graph (counter reset + launch) and replayed.
