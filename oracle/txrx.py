@@ -20,8 +20,24 @@
   so its total-derivative contribution vanishes), and the matched filter is
   real and even, hence self-adjoint.
 
+* Receiver front end (Sec. IV-A, Table I): the channel is simulated at
+  rho_a > rho_d samples/symbol; the received waveform is low-pass filtered by
+  an ideal brick-wall filter of bandwidth Delta B and sampled at t = k / f_s.
+  Both grids span the same period N_sym / R_s, so DFT bin kappa is the same
+  frequency kappa R_s / N_sym on either grid.  Readings: Delta B is the total
+  (two-sided) bandwidth and Table I's Delta B = f_s is taken (the text's 2 f_s
+  would alias at t = k / f_s; the 37.5 GHz of the 32 GBd WDM case only makes
+  sense two-sided); the passband is open, |f| < Delta B / 2, so at
+  Delta B = f_s the Nyquist bin of the sampled grid is rejected.  The same
+  band limit defines the opposite direction, band-limited interpolation of a
+  DSP-rate waveform onto the analog grid.
+
 Pins: back-to-back recovery s_hat = s, Parseval power of the TX waveform,
-finite differences of the loss, AWGN SNR estimator.
+finite differences of the loss, AWGN SNR estimator; front end: single-tone
+closed forms (pass, reject, no alias, band edge), rho_a-rate TX sampled down
+equals rho_d-rate TX, gamma = 0 propagation commutes with the front end, ASE
+power after the front end independent of the simulation rate, interpolation
+round trip.
 """
 from __future__ import annotations
 
@@ -98,3 +114,47 @@ def loss_grad(y, s, sps: int, rolloff: float, power_w):
     up[:, ::sps] = g_z / np.sqrt(p * sps)[:, None]
     H = rrc_response(n, sps, rolloff)
     return np.fft.ifft(np.fft.fft(up, axis=-1) * H, axis=-1), ev
+
+
+def brickwall_mask(n: int, band_bins: float):
+    """Ideal low-pass on an n-bin DFT grid: 1 where |kappa| < band_bins / 2 (kappa signed, fftfreq order)."""
+    kappa = np.fft.fftfreq(n) * n
+    return (np.abs(kappa) < band_bins / 2.0).astype(np.float64)
+
+
+def lowpass_sample(y, n_out: int, bandwidth: float = 1.0):
+    """Receiver front end (Sec. IV-A): brick-wall low-pass, then sampling at t = k / f_s.
+
+    y [B, n_in] on the analog grid (rho_a samples/symbol), n_out = rho_d N_sym
+    with n_in a multiple of n_out.  Delta B = bandwidth * f_s spans
+    bandwidth * n_out bins.  The filtered waveform is formed on the analog grid
+    and every (n_in / n_out)-th sample is kept, offset 0.
+    """
+    y = np.atleast_2d(np.asarray(y, dtype=np.complex128))
+    n_in = y.shape[-1]
+    if n_out < 1 or n_in % n_out:
+        raise ValueError("n_in must be a multiple of n_out")
+    if not 0.0 < bandwidth <= 1.0:
+        raise ValueError("bandwidth must be in (0, 1]")
+    mask = brickwall_mask(n_in, bandwidth * n_out)
+    z = np.fft.ifft(np.fft.fft(y, axis=-1) * mask, axis=-1)
+    return z[:, :: n_in // n_out]
+
+
+def interpolate(x, n_out: int):
+    """Band-limited periodic interpolation of x [B, n_in] onto n_out >= n_in points.
+
+    The samples at t = m T / n_out of the trigonometric polynomial with bins
+    |kappa| < n_in / 2 that takes the values x at t = k T / n_in (the Nyquist
+    bin, whose frequency sign is ambiguous, is left out).  n_out is a multiple
+    of n_in.
+    """
+    x = np.atleast_2d(np.asarray(x, dtype=np.complex128))
+    B, n_in = x.shape
+    if n_out % n_in:
+        raise ValueError("n_out must be a multiple of n_in")
+    X = np.fft.fft(x, axis=-1) * brickwall_mask(n_in, n_in)
+    kappa = np.rint(np.fft.fftfreq(n_in) * n_in).astype(np.int64)
+    Y = np.zeros((B, n_out), dtype=np.complex128)
+    Y[:, kappa % n_out] = X * (n_out / n_in)
+    return np.fft.ifft(Y, axis=-1)
