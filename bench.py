@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=B, help="waveforms per GPU (profiling runs use fewer)")
     ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft", "ldbp_bwd", "channel"],
                     help="run only this kernel (warmup + steps launches) on random input, for ncu captures")
-    ap.add_argument("--workload", default="ldbp", choices=["ldbp", "channel", "ragged", "train", "sym32", "essm"],
+    ap.add_argument("--workload", default="ldbp", choices=["ldbp", "channel", "ragged", "train", "sym32", "essm", "analog"],
                     help="ldbp: the headline; channel / ragged / train: the other workloads, reported separately")
     return ap.parse_args()
 
@@ -457,6 +457,57 @@ def workload_sym32(args, api):
                       "model": "LS-initialised (untrained)", **res}))
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth of this GPU model (measured copy), else the fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, "fallback"
+
+
+def workload_analog(args, api):
+    """Analog-rate system model of Sec. IV-A: 64 waveforms of 32768 16-QAM symbols at
+    10 GBd simulated at rho_a = 6 samples/symbol (n = 196608) over 25 x 80 km (100
+    symmetric steps/span, ASE) on the library-FFT split-step path, then brick-wall
+    low-pass (Delta B = f_s) and sampling at rho_d = 2.  Reports the front end's
+    throughput against HBM (algorithmic bytes: one read of the input grid, one write
+    of the output grid), the channel's throughput, and the effective SNR of 1-StPS
+    DBP on the received samples compared with the same link simulated at rho_d."""
+    import torch
+    import synth
+    Bw, nsym, rho_a, rho_d, Rs = 64, 32768, 6, 2, FS / 2
+    n_a, n_d = nsym * rho_a, nsym * rho_d
+    fib = synth.Fiber()
+    link = synth.Link(M_STEPS, SPAN_KM, 100, True, True, 5.0, 1.946e14, seed=78, counter=0)
+    sym = torch.from_numpy(synth.qam16_symbols(Bw, nsym, 3000).astype(np.complex64)).cuda()
+    pw = torch.full((Bw,), 1e-3 * 10 ** (POWER_DBM / 10), dtype=torch.float32, device="cuda")
+    xd = api.tx(sym, pw, sps=rho_d)
+    xa = api.resample(xd, n_a)
+    ya = torch.empty_like(xa)
+    r = torch.empty_like(xd)
+    ws = torch.empty(n_a * Bw * 8, dtype=torch.uint8, device="cuda")
+    ch_ms = time_fn(lambda: api.ssm_cufft(fib, link, rho_a * Rs, xa, out=ya), 2, 1)
+    down_ms = time_fn(lambda: api.resample(ya, n_d, out=r, workspace=ws), 20, 3)
+    up_ms = time_fn(lambda: api.resample(xd, n_a, out=xa, workspace=ws), 20, 3)
+    peak, kind = measured_hbm_gbs()
+    alg = (n_a + n_d) * 8 * Bw
+    dbp_a = api.dbp_apply(fib, link, FS, r, 1, False)
+    st_a, _, _ = api.rx(dbp_a, sym, pw)
+    yd = api.ssm_forward(fib, link, FS, xd)
+    dbp_d = api.dbp_apply(fib, link, FS, yd, 1, False)
+    st_d, _, _ = api.rx(dbp_d, sym, pw)
+    print(json.dumps({"workload": f"analog_rate_{Bw}x{nsym}sym_rho6_to_rho2_25x80km_100stps", "unit": UNIT,
+                      "channel_ms": ch_ms,
+                      "channel_samples_steps_per_s": Bw * n_a * M_STEPS * 100 / (ch_ms / 1e3),
+                      "front_end_down_ms": down_ms, "front_end_up_ms": up_ms,
+                      "front_end_input_samples_per_s": Bw * n_a / (down_ms / 1e3),
+                      "front_end_roofline": {"bound": "hbm", "achieved": alg / (down_ms / 1e3) / 1e9, "peak": peak,
+                                             "unit": "GB/s", "frac": alg / (down_ms / 1e3) / 1e9 / peak,
+                                             "peak_kind": kind,
+                                             "algorithmic_bytes": "8 (n_in + n_out) per waveform"},
+                      "dbp_1stps_snr_db_rho_a6": api.snr_db(st_a), "dbp_1stps_snr_db_rho_d2": api.snr_db(st_d)}))
+
+
 def workload_essm(args, api):
     """Learned enhanced SSM (filtered nonlinear steps, Sec. III-C): the LDBP inference
     workload (256 x 65536, 25 x 80 km at 2 dBm, GPU channel data) with a (2 kappa + 1)-tap
@@ -542,6 +593,8 @@ def main():
         return workload_sym32(args, api)
     if args.workload == "essm":
         return workload_essm(args, api)
+    if args.workload == "analog":
+        return workload_analog(args, api)
 
     fib = synth.Fiber()
     t_setup = time.perf_counter()

@@ -376,7 +376,9 @@ int dbp_apply(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, int3
  * an inverse FFT and a Kerr kernel.  Provided only as the library-FFT
  * comparison for the fused kernel; results agree with ssm_forward/dbp_apply
  * to FP32 rounding.  cuFFT allocates its own work area on the first call for
- * a given (n, batch).  Arguments and errors as ssm_forward.
+ * a given (stream, n, batch).  Arguments and errors as ssm_forward, except
+ * that n may be any length in [2, 2^27] (e.g. the 6 samples/symbol grids of
+ * the analog-rate simulation of Sec. IV-A, Table I).
  */
 int ssm_cufft(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, int32_t dbp_steps_per_span,
               int32_t dbp_symmetric, const void* x, void* y, int64_t n, int32_t batch, void* stream);
@@ -418,6 +420,38 @@ int ldbp_tx(const void* symbols, const float* power_w, int32_t sps, double rollo
  */
 int ldbp_rx(const void* y, const void* symbols, const float* power_w, int32_t sps, double rolloff, int64_t nsym,
             int32_t batch, double* stats, float* phi, void* grad, float grad_scale, void* workspace, void* stream);
+
+/*
+ * ldbp_resample -- receiver front end of Sec. IV-A (Table I) and its inverse.
+ *
+ * The channel is simulated at rho_a samples/symbol (n_in = rho_a N_sym); the
+ * received waveform passes an ideal brick-wall low-pass of total bandwidth
+ * Delta B and is sampled at t = k / f_s (n_out = rho_d N_sym).  Both grids
+ * span the same period N_sym / R_s, so DFT bin kappa (signed, fftfreq order)
+ * is the same frequency on either, and
+ *   y_b[m] = (1 / n_in) sum_{|kappa| < bandwidth n_c / 2} X_b[kappa] e^{j 2 pi kappa m / n_out},
+ *   X_b = DFT(x_b) (unnormalised), n_c = min(n_in, n_out),
+ * i.e. the low-passed waveform sampled at the output rate.  bandwidth is
+ * Delta B relative to the coarser grid's sample rate; 1 is Table I's
+ * Delta B = f_s.  The passband is open, so at bandwidth 1 the Nyquist bin is
+ * rejected.  With n_out > n_in the same formula is band-limited interpolation
+ * onto a finer grid (e.g. a DSP-rate transmit waveform onto the analog grid).
+ *  x          device complex64 [batch][n_in], 16-byte aligned
+ *  y          device complex64 [batch][n_out] (output), 16-byte aligned; may
+ *             alias x
+ *  n_in, n_out  in [2, 2^27]; one divides the other
+ *  bandwidth  in (0, 1]
+ *  workspace  device, >= ldbp_resample_workspace(n_in, batch) bytes, 16-byte
+ *             aligned, overlapping neither x nor y; owned by the caller
+ * Asynchronous on stream: a cuFFT forward transform (n_in), a passband gather
+ * kernel, a cuFFT inverse transform (n_out).  cuFFT allocates its own work
+ * area on the first call for a given (stream, n, batch).
+ * Errors: LDBP_EINVAL (NULL pointer, sizes, misalignment, overlap, bandwidth
+ * out of range), LDBP_ENONFINITE (bandwidth NaN or infinite), LDBP_ECUDA.
+ */
+size_t ldbp_resample_workspace(int64_t n_in, int32_t batch);
+int ldbp_resample(const void* x, int64_t n_in, void* y, int64_t n_out, double bandwidth, int32_t batch,
+                  void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * ldbp_ubench -- arithmetic ceilings of the current device (synchronous).

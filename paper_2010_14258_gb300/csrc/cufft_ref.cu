@@ -1,13 +1,17 @@
 // Library-FFT split-step (cuFFT + elementwise kernels), the comparison path
 // for the fused cluster-resident kernel.  Runs the same FP64-built programs
 // step by step: forward FFT, spectral multiply (+ ASE), inverse FFT, Kerr.
+// cuFFT takes any length, so this path also simulates the non-power-of-two
+// grids of the analog-rate channel (e.g. 6 samples/symbol).
 #include <cufft.h>
 
+#include <cstdio>
 #include <map>
 #include <mutex>
 #include <string>
 
 #include "common.cuh"
+#include "cufft_plan.cuh"
 #include "philox.cuh"
 #include "ssm_host.cuh"
 
@@ -39,24 +43,29 @@ __global__ void kerr_kernel(float2* __restrict__ x, float c, long long total) {
 static std::mutex g_plan_mu;
 static std::map<std::string, cufftHandle> g_plans;
 
-static int get_plan(long long n, int batch, cufftHandle* out) {
+int cufft_plan(long long n, int batch, cudaStream_t st, cufftHandle* out) {
   int dev = 0;
   LDBP_CUDA_TRY(cudaGetDevice(&dev));
-  const std::string key = std::to_string(dev) + ":" + std::to_string(n) + ":" + std::to_string(batch);
+  char key[96];
+  snprintf(key, sizeof(key), "%d:%p:%lld:%d", dev, (void*)st, n, batch);
   std::lock_guard<std::mutex> lk(g_plan_mu);
   auto it = g_plans.find(key);
-  if (it != g_plans.end()) {
-    *out = it->second;
-    return 0;
+  if (it == g_plans.end()) {
+    cufftHandle h;
+    long long nn = n;
+    size_t ws = 0;
+    if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(LDBP_ECUDA, "cufftCreate failed");
+    if (cufftMakePlanMany64(h, 1, &nn, nullptr, 1, n, nullptr, 1, n, CUFFT_C2C, batch, &ws) != CUFFT_SUCCESS) {
+      cufftDestroy(h);
+      return fail(LDBP_ECUDA, "cufftMakePlanMany64 failed for n=%lld batch=%d", n, batch);
+    }
+    if (cufftSetStream(h, st) != CUFFT_SUCCESS) {
+      cufftDestroy(h);
+      return fail(LDBP_ECUDA, "cufftSetStream failed");
+    }
+    it = g_plans.emplace(key, h).first;
   }
-  cufftHandle h;
-  long long nn = n;
-  size_t ws = 0;
-  if (cufftCreate(&h) != CUFFT_SUCCESS) return fail(LDBP_ECUDA, "cufftCreate failed");
-  if (cufftMakePlanMany64(h, 1, &nn, nullptr, 1, n, nullptr, 1, n, CUFFT_C2C, batch, &ws) != CUFFT_SUCCESS)
-    return fail(LDBP_ECUDA, "cufftMakePlanMany64 failed for n=%lld batch=%d", n, batch);
-  g_plans[key] = h;
-  *out = h;
+  *out = it->second;
   return 0;
 }
 
@@ -66,14 +75,13 @@ using namespace ldbp;
 
 extern "C" int ssm_cufft(const ldbp_fiber* fiber, const ldbp_link* link, double fs_hz, int32_t dbp_steps_per_span,
                          int32_t dbp_symmetric, const void* x, void* y, int64_t n, int32_t batch, void* stream) {
-  if (int rc = check_link(fiber, link, fs_hz, x, y, n, batch)) return rc;
+  if (int rc = check_link(fiber, link, fs_hz, x, y, n, batch, /*pow2=*/false)) return rc;
   if (dbp_steps_per_span < 0) return fail(LDBP_EINVAL, "dbp_steps_per_span must be >= 0");
   std::shared_ptr<DeviceProgram> dp;
   if (int rc = link_program(*fiber, *link, fs_hz, n, dbp_steps_per_span, dbp_symmetric != 0, &dp)) return rc;
-  cufftHandle plan;
-  if (int rc = get_plan(n, batch, &plan)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (cufftSetStream(plan, st) != CUFFT_SUCCESS) return fail(LDBP_ECUDA, "cufftSetStream failed");
+  cufftHandle plan;
+  if (int rc = cufft_plan(n, batch, st, &plan)) return rc;
   const long long total = n * (long long)batch;
   float2* Y = static_cast<float2*>(y);
   if (x != y) LDBP_CUDA_TRY(cudaMemcpyAsync(y, x, total * sizeof(float2), cudaMemcpyDeviceToDevice, st));

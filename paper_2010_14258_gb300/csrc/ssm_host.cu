@@ -200,7 +200,7 @@ static std::string fkey(const ldbp_fiber& f, double fs, long long n) {
 }
 
 int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x, const void* y, long long n,
-                      int batch) {
+               int batch, bool pow2) {
   if (!f || !l || !x || !y) return fail(LDBP_EINVAL, "fiber, link, x and y must be non-NULL");
   if (!std::isfinite(fs)) return fail(LDBP_ENONFINITE, "fs_hz is NaN or infinite");
   if (!(fs > 0.0)) return fail(LDBP_EINVAL, "fs_hz must be positive");
@@ -211,9 +211,12 @@ int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x
   if (l->n_spans < 1 || !(l->span_km > 0.0) || l->steps_per_span < 1)
     return fail(LDBP_EINVAL, "link needs n_spans >= 1, span_km > 0, steps_per_span >= 1");
   if (batch < 1) return fail(LDBP_EINVAL, "batch=%d must be >= 1", batch);
-  if (n < (1LL << kSsmMinLogN2) || n > (1LL << (kSsmMaxLogN2 + 4)) || (n & (n - 1)))
+  if (!pow2) {
+    if (n < 2 || n > (1LL << 27)) return fail(LDBP_EINVAL, "n=%lld must be in [2, 2^27]", n);
+  } else if (n < (1LL << kSsmMinLogN2) || n > (1LL << (kSsmMaxLogN2 + 4)) || (n & (n - 1))) {
     return fail(LDBP_EINVAL, "n=%lld must be a power of two in [%d, %d]", n, 1 << kSsmMinLogN2,
                 1 << (kSsmMaxLogN2 + 4));
+  }
   if ((long long)l->n_spans * l->steps_per_span > 1000000) return fail(LDBP_EINVAL, "too many steps");
   return 0;
 }

@@ -101,3 +101,36 @@ def _essm(L, kappa=(2,), stride=5, eta=ctypes.c_void_p(64), T=(3,)):
 def test_ldbp_essm_apply_rejects(L, kw, needle):
     assert _essm(L, **kw) == -1
     assert needle in L.ldbp_last_error().decode()
+
+
+def _resample(L, **kw):
+    args = dict(x=ctypes.c_void_p(4096), n_in=384, y=ctypes.c_void_p(1 << 22), n_out=128, bw=1.0, B=2,
+                ws=ctypes.c_void_p(1 << 24), wsb=384 * 2 * 8)
+    args.update(kw)
+    return L.ldbp_resample(args["x"], args["n_in"], args["y"], args["n_out"], args["bw"], args["B"], args["ws"],
+                           args["wsb"], None)
+
+
+def test_resample_workspace_size(L):
+    assert L.ldbp_resample_workspace(384, 2) == 384 * 2 * 8
+    assert L.ldbp_resample_workspace(1, 2) == 0
+
+
+@pytest.mark.parametrize("kw, needle", [
+    (dict(x=None), "non-NULL"),
+    (dict(bw=0.0), "bandwidth"),
+    (dict(bw=1.5), "bandwidth"),
+    (dict(n_out=100), "divide"),
+    (dict(n_in=1), "n_in=1"),
+    (dict(B=0), "batch=0"),
+    (dict(wsb=100), "workspace"),
+    (dict(ws=ctypes.c_void_p((1 << 24) + 8)), "aligned"),
+    (dict(ws=ctypes.c_void_p(4096 + 64)), "overlaps"),
+])
+def test_resample_rejects(L, kw, needle):
+    assert _resample(L, **kw) == -1
+    assert needle in L.ldbp_last_error().decode()
+
+
+def test_resample_rejects_nonfinite_bandwidth(L):
+    assert _resample(L, bw=float("nan")) == -6

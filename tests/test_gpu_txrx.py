@@ -74,3 +74,67 @@ def test_cufft_path_matches_oracle(mode):
         ref = nlse.dbp(x, fib, link, fs, steps_per_span=2, symmetric=sym)
     torch.cuda.synchronize()
     assert rel_l2(to_np(out), ref) <= 1e-4
+
+
+@pytest.mark.parametrize("B,n_out,r,bw", [(3, 1024, 3, 1.0), (2, 1024, 3, 0.6), (1, 333, 3, 1.0), (2, 512, 4, 0.5),
+                                          (2, 256, 1, 0.8)])
+def test_resample_down_matches_oracle(B, n_out, r, bw):
+    # brick-wall low-pass + sampling at the DSP rate (Sec. IV-A), wideband input
+    # so that the filter cuts; odd grids and the plain low-pass (r = 1) included
+    import torch
+    api = _api()
+    x = c64(synth.gaussian_waveform(B, n_out * r, 40 + B, 1.0))
+    y = api.resample(to_dev(x), n_out, bw)
+    torch.cuda.synchronize()
+    assert rel_l2(to_np(y), txrx.lowpass_sample(x, n_out, bw)) <= 2e-6
+
+
+@pytest.mark.parametrize("B,n_in,r", [(3, 1024, 3), (1, 333, 3), (2, 256, 8)])
+def test_resample_up_matches_oracle(B, n_in, r):
+    import torch
+    api = _api()
+    x = c64(synth.gaussian_waveform(B, n_in, 50 + B, 1.0))
+    y = api.resample(to_dev(x), n_in * r)
+    torch.cuda.synchronize()
+    assert rel_l2(to_np(y), txrx.interpolate(x, n_in * r)) <= 2e-6
+
+
+@pytest.mark.parametrize("symmetric,ase", [(True, True), (False, False)])
+def test_analog_rate_link_matches_oracle(symmetric, ase):
+    # The system model of Sec. IV-A: transmit waveform on the analog grid
+    # (rho_a = 6 samples/symbol, here interpolated from the DSP-rate transmitter),
+    # split-step channel on that non-power-of-two grid, brick-wall low-pass and
+    # sampling at rho_d = 2.  Oracle: the same chain in FP64 at rho_a.
+    import torch
+    api = _api()
+    B, nsym, rho_a, rho_d, Rs = 2, 512, 6, 2, 10e9
+    s = c64(synth.qam16_symbols(B, nsym, 21))
+    P = np.array([1.585e-3, 3e-3], np.float32)
+    fib = synth.Fiber()
+    link = synth.Link(2, 80.0, 6, symmetric, ase, seed=9, counter=1)
+    xd = api.tx(to_dev(s), torch.from_numpy(P).cuda(), sps=rho_d)
+    xa = api.resample(xd, nsym * rho_a)
+    ya = api.ssm_cufft(fib, link, rho_a * Rs, xa)
+    r = api.resample(ya, nsym * rho_d)
+    torch.cuda.synchronize()
+    ref = txrx.lowpass_sample(nlse.channel(txrx.tx(s, rho_a, 0.1, P.astype(np.float64)), fib, link, rho_a * Rs),
+                              nsym * rho_d)
+    assert rel_l2(to_np(r), ref) <= 1e-4
+
+
+def test_resample_full_size_sampled_waveforms():
+    # 64 waveforms of 32768 symbols at rho_a = 6 (n = 196608) down to rho_d = 2
+    # and back up; waveforms 0 and 63 against the oracle.
+    import torch
+    api = _api()
+    B, nsym = 64, 32768
+    g = torch.Generator(device="cuda").manual_seed(61)
+    x = torch.randn(B, 6 * nsym, dtype=torch.complex64, device="cuda", generator=g)
+    y = api.resample(x, 2 * nsym)
+    z = api.resample(y, 6 * nsym)
+    torch.cuda.synchronize()
+    for b in (0, B - 1):
+        xb = to_np(x[b:b + 1])
+        ref = txrx.lowpass_sample(xb, 2 * nsym)
+        assert rel_l2(to_np(y[b:b + 1]), ref) <= 2e-6
+        assert rel_l2(to_np(z[b:b + 1]), txrx.interpolate(ref, 6 * nsym)) <= 4e-6
