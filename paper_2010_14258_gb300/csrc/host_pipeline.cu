@@ -17,7 +17,7 @@ constexpr int kMaxChunks = 256;
 // Library-owned streams and events, created once per device.
 struct PipeStreams {
   cudaStream_t in = nullptr, cmp[2] = {nullptr, nullptr}, out = nullptr;
-  cudaEvent_t start = nullptr, done = nullptr;
+  cudaEvent_t start = nullptr, join[4] = {};
   cudaEvent_t ev_in[kMaxChunks] = {}, ev_cmp[kMaxChunks] = {};
   bool ready = false;
 };
@@ -35,7 +35,7 @@ cudaError_t pipe_streams(int dev, PipeStreams** out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps.cmp[1], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps.out, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ps.start, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ps.done, cudaEventDisableTiming);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ps.join[i], cudaEventDisableTiming);
     for (int i = 0; i < kMaxChunks && e == cudaSuccess; ++i) {
       e = cudaEventCreateWithFlags(&ps.ev_in[i], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ps.ev_cmp[i], cudaEventDisableTiming);
@@ -45,6 +45,27 @@ cudaError_t pipe_streams(int dev, PipeStreams** out) {
   }
   *out = &ps;
   return cudaSuccess;
+}
+
+// Enqueues every chunk: copy-in on `in`, the pass on one of the two compute
+// streams, copy-out on `out`, ordered by events.
+int enqueue_chunks(PipeStreams* ps, const void* taps, int32_t taps_stride, const int32_t* T, const float* c, int32_t M,
+                   const char* xh, char* yh, char* xd, char* yd, int64_t n, int32_t batch, int32_t chunks, size_t row) {
+  for (int i = 0; i < chunks; ++i) {
+    const long long a = (long long)batch * i / chunks, b = (long long)batch * (i + 1) / chunks;
+    if (b <= a) continue;
+    const size_t off = row * (size_t)a, len = row * (size_t)(b - a);
+    LDBP_CUDA_TRY(cudaMemcpyAsync(xd + off, xh + off, len, cudaMemcpyHostToDevice, ps->in));
+    LDBP_CUDA_TRY(cudaEventRecord(ps->ev_in[i], ps->in));
+    cudaStream_t cs = ps->cmp[i & 1];  // two compute streams: a chunk's last wave overlaps the next chunk
+    LDBP_CUDA_TRY(cudaStreamWaitEvent(cs, ps->ev_in[i], 0));
+    if (int rc = ldbp_apply(taps, taps_stride, T, c, M, xd + off, yd + off, n, (int32_t)(b - a), nullptr, cs))
+      return rc;
+    LDBP_CUDA_TRY(cudaEventRecord(ps->ev_cmp[i], cs));
+    LDBP_CUDA_TRY(cudaStreamWaitEvent(ps->out, ps->ev_cmp[i], 0));
+    LDBP_CUDA_TRY(cudaMemcpyAsync(yh + off, yd + off, len, cudaMemcpyDeviceToHost, ps->out));
+  }
+  return LDBP_OK;
 }
 
 }  // namespace
@@ -86,22 +107,19 @@ int ldbp_apply_host(const void* taps, int32_t taps_stride, const int32_t* T, con
   LDBP_CUDA_TRY(cudaStreamWaitEvent(ps->cmp[0], ps->start, 0));
   LDBP_CUDA_TRY(cudaStreamWaitEvent(ps->cmp[1], ps->start, 0));
   LDBP_CUDA_TRY(cudaStreamWaitEvent(ps->out, ps->start, 0));
-  for (int i = 0; i < chunks; ++i) {
-    const long long a = (long long)batch * i / chunks, b = (long long)batch * (i + 1) / chunks;
-    if (b <= a) continue;
-    const size_t off = row * (size_t)a, len = row * (size_t)(b - a);
-    LDBP_CUDA_TRY(cudaMemcpyAsync(xd + off, xh + off, len, cudaMemcpyHostToDevice, ps->in));
-    LDBP_CUDA_TRY(cudaEventRecord(ps->ev_in[i], ps->in));
-    cudaStream_t cs = ps->cmp[i & 1];  // two compute streams: a chunk's last wave overlaps the next chunk
-    LDBP_CUDA_TRY(cudaStreamWaitEvent(cs, ps->ev_in[i], 0));
-    if (int rc = ldbp_apply(taps, taps_stride, T, c, M, xd + off, yd + off, n, (int32_t)(b - a), nullptr, cs))
-      return rc;
-    LDBP_CUDA_TRY(cudaEventRecord(ps->ev_cmp[i], cs));
-    LDBP_CUDA_TRY(cudaStreamWaitEvent(ps->out, ps->ev_cmp[i], 0));
-    LDBP_CUDA_TRY(cudaMemcpyAsync(yh + off, yd + off, len, cudaMemcpyDeviceToHost, ps->out));
+  const int rc = enqueue_chunks(ps, taps, taps_stride, T, c, M, xh, yh, xd, yd, n, batch, chunks, row);
+  // The caller's stream waits for all four library streams, also after a
+  // failure part-way, so no copy of an already enqueued chunk outlives the
+  // call's place in the caller's stream order.
+  cudaStream_t lib_streams[4] = {ps->in, ps->cmp[0], ps->cmp[1], ps->out};
+  cudaError_t je = cudaSuccess;
+  for (int i = 0; i < 4; ++i) {
+    cudaError_t e = cudaEventRecord(ps->join[i], lib_streams[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ps->join[i], 0);
+    if (e != cudaSuccess && je == cudaSuccess) je = e;
   }
-  LDBP_CUDA_TRY(cudaEventRecord(ps->done, ps->out));
-  LDBP_CUDA_TRY(cudaStreamWaitEvent(st, ps->done, 0));
+  if (rc != LDBP_OK) return rc;
+  if (je != cudaSuccess) return cuda_fail(je, "joining the pipeline streams");
   return LDBP_OK;
 }
 
