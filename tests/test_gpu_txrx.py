@@ -138,3 +138,37 @@ def test_resample_full_size_sampled_waveforms():
         ref = txrx.lowpass_sample(xb, 2 * nsym)
         assert rel_l2(to_np(y[b:b + 1]), ref) <= 2e-6
         assert rel_l2(to_np(z[b:b + 1]), txrx.interpolate(ref, 6 * nsym)) <= 4e-6
+
+
+def test_receiver_serves_the_validated_equaliser():
+    # Receiver with full-length DBP as the fallback of LDBP: the served output is
+    # bit-identical to ldbp_apply when validation accepts LDBP and to dbp_apply
+    # otherwise; the validation SNRs are those of the receiver chain on each.
+    import torch
+    api = _api()
+    from paper_2010_14258_gb300 import init, receiver
+    fs, pw = 20e9, 10 ** (2.0 / 10) * 1e-3
+    fib = synth.Fiber()
+    link = synth.Link(25, 80.0, 4, True, False)
+    s = to_dev(c64(synth.qam16_symbols(2, 4096, 31)))
+    p = torch.full((2,), pw, dtype=torch.float32, device="cuda")
+    y = api.ssm_forward(fib, link, fs, api.tx(s, p))
+    Ts = [9] * 25
+    taps, c = init.ldbp_init(Ts, span_km=80.0, fs=fs)
+    tp = np.zeros((25, 5), np.complex64)
+    for i, h in enumerate(taps):
+        tp[i, : len(h)] = h
+    td = torch.from_numpy(tp).cuda()
+    ref_l = api.ldbp_apply(td, Ts, c, y)
+    ref_d = api.dbp_apply(fib, link, fs, y, 1, False)
+    st_l, _, _ = api.rx(ref_l, s, p)
+    st_d, _, _ = api.rx(ref_d, s, p)
+    for tol, use in ((1e3, True), (-1e3, False)):
+        r = receiver.Receiver(td, Ts, c, fib, link, fs, tolerance_db=tol)
+        d = r.validate(y, s, p)
+        assert d.use_ldbp is use
+        assert abs(d.snr_ldbp_db - api.snr_db(st_l)) <= 1e-9
+        assert abs(d.snr_dbp_db - api.snr_db(st_d)) <= 1e-9
+        out = r.backpropagate(y)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref_l if use else ref_d)

@@ -62,3 +62,57 @@ def test_binding_rejects_bad_tensors_before_any_launch():
         api.ldbp_essm_apply(taps, [3, 3], [0.0, 0.0], torch.zeros(2, 3), [1, 1], x)  # eta not on a GPU
     with pytest.raises(ValueError):
         api.ldbp_apply_host(taps, [3, 3], [0.0, 0.0], x.to(torch.complex128), x)  # not complex64
+
+
+class _FakeBackend:
+    """Stands in for the library: tags which equaliser ran and reports set SNRs."""
+
+    def __init__(self, snr_ldbp, snr_dbp):
+        self.snr = {"ldbp": snr_ldbp, "dbp": snr_dbp}
+        self.calls = []
+
+    def ldbp_apply(self, taps, T, c, y):
+        self.calls.append("ldbp")
+        return ("ldbp", y)
+
+    def dbp_apply(self, fiber, link, fs, y, steps, symmetric):
+        self.calls.append("dbp")
+        return ("dbp", y)
+
+    def rx(self, z, symbols, power_w, sps=2, rolloff=0.1):
+        return z[0], None, None
+
+    def snr_db(self, stats):
+        return self.snr[stats]
+
+
+def _receiver(snr_ldbp, snr_dbp, tol=0.1):
+    from paper_2010_14258_gb300 import receiver
+    be = _FakeBackend(snr_ldbp, snr_dbp)
+    return receiver.Receiver(None, [3], [0.0], None, None, 20e9, tolerance_db=tol, backend=be), be
+
+
+def test_receiver_falls_back_to_dbp_until_validated():
+    r, be = _receiver(25.9, 25.7)
+    assert not r.uses_ldbp
+    assert r.backpropagate("y")[0] == "dbp"
+
+
+@pytest.mark.parametrize("snr_ldbp, snr_dbp, use", [(25.9, 25.7, True), (25.6, 25.7, True),
+                                                     (25.5, 25.7, False), (19.0, 25.7, False)])
+def test_receiver_uses_ldbp_only_within_the_tolerance(snr_ldbp, snr_dbp, use):
+    r, be = _receiver(snr_ldbp, snr_dbp)
+    d = r.validate("y", "s", 1e-3)
+    assert (d.snr_ldbp_db, d.snr_dbp_db) == (snr_ldbp, snr_dbp)
+    assert be.calls == ["ldbp", "dbp"]
+    assert r.uses_ldbp is use
+    assert r.backpropagate("y")[0] == ("ldbp" if use else "dbp")
+
+
+def test_receiver_revalidation_can_withdraw_the_model():
+    r, be = _receiver(25.9, 25.7)
+    r.validate("y", "s", 1e-3)
+    assert r.uses_ldbp
+    be.snr["ldbp"] = 20.0  # e.g. the link changed
+    r.validate("y", "s", 1e-3)
+    assert not r.uses_ldbp and r.backpropagate("y")[0] == "dbp"
