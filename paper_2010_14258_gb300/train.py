@@ -19,6 +19,7 @@ unit filters (h = (1, 0, ..., 0), link-agnostic) and random filters
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
 
 import numpy as np
@@ -61,6 +62,15 @@ class TrainConfig:
     @property
     def n(self):
         return self.nsym * self.sps
+
+
+def iteration_record(step: int, loss: float, lr: float, T) -> dict:
+    """One line of the training log.  The loss is the batch-mean ||s_hat - s||^2 / N_sym
+    with E|s|^2 = 1, so 10 log10(1 / loss) is the batch's effective SNR (Eq. (14))
+    up to the sample mean of |s|^2."""
+    snr = 10.0 * math.log10(1.0 / loss) if loss > 0 else float("inf")
+    return {"step": int(step), "loss": float(loss), "snr_db": snr, "lr": float(lr),
+            "taps": int(sum(T)), "T": [int(t) for t in T]}
 
 
 def pruning_schedule(total_steps: int, iters: int, frac: float):
@@ -208,11 +218,21 @@ class Trainer:
         if best >= 0:
             self.T[best] -= 2
 
-    def fit(self, iters=None, log_every=0):
-        for it in range(iters or self.cfg.iters):
-            loss = self.train_step(it)
-            if log_every and it % log_every == 0:
-                print(f"it {it:5d} loss {loss:.4e} snr {10 * np.log10(1 / loss):.2f} dB taps {sum(self.T)}")
+    def fit(self, iters=None, log_every=0, log_path=None):
+        """Runs the iterations; with log_path, appends one JSON line per iteration
+        (iteration, loss, effective SNR of the batch, learning rate, filter lengths)."""
+        log = open(log_path, "a") if log_path else None
+        try:
+            for it in range(iters or self.cfg.iters):
+                loss = self.train_step(it)
+                rec = iteration_record(self.step_count, loss, self.lr_at(it), self.T)
+                if log is not None:
+                    log.write(json.dumps(rec) + "\n")
+                if log_every and it % log_every == 0:
+                    print(f"it {it:5d} loss {loss:.4e} snr {rec['snr_db']:.2f} dB taps {rec['taps']}")
+        finally:
+            if log is not None:
+                log.close()
         return self.history
 
     # ------------------------------------------------------------------ evaluation

@@ -116,3 +116,10 @@ def test_receiver_revalidation_can_withdraw_the_model():
     be.snr["ldbp"] = 20.0  # e.g. the link changed
     r.validate("y", "s", 1e-3)
     assert not r.uses_ldbp and r.backpropagate("y")[0] == "dbp"
+
+
+def test_training_log_record():
+    import json
+    rec = train.iteration_record(7, 1e-2, 5e-4, [9, 7, 5])
+    assert rec == {"step": 7, "loss": 1e-2, "snr_db": 20.0, "lr": 5e-4, "taps": 21, "T": [9, 7, 5]}
+    assert json.loads(json.dumps(rec)) == rec
