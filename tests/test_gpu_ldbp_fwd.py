@@ -241,8 +241,8 @@ def test_ldbp_effective_snr_matches_oracle():
     Ts = [9] * 25
     taps, c = _model(Ts, seed=23)
     y, _ = _run(taps, Ts, c, r)
-    ref, _ = oldbp.forward(r, taps, c)
-    assert rel_l2(y, ref) <= 1e-4
+    ref, floor = fp32_floor(r, taps, c)
+    assert rel_l2(y, ref) <= max(1e-4, 10 * floor)
     snr_gpu = txrx.evaluate(y, s, 2, 0.1, pw)["snr_db"]
     snr_ref = txrx.evaluate(ref, s, 2, 0.1, pw)["snr_db"]
     assert abs(snr_gpu - snr_ref) <= 0.01
