@@ -134,3 +134,36 @@ def test_resample_rejects(L, kw, needle):
 
 def test_resample_rejects_nonfinite_bandwidth(L):
     assert _resample(L, bw=float("nan")) == -6
+
+
+def _split_step(L, fn, n, **kw):
+    import synth
+    from paper_2010_14258_gb300 import api
+    f = api.fiber_struct(synth.Fiber(**kw.pop("fiber", {})))
+    lk = api.link_struct(synth.Link(**kw.pop("link", {})))
+    x, y = ctypes.c_void_p(4096), ctypes.c_void_p(1 << 22)
+    if fn == "ssm_forward":
+        return L.ssm_forward(ctypes.byref(f), ctypes.byref(lk), 20e9, x, y, n, 1, None)
+    return L.ssm_cufft(ctypes.byref(f), ctypes.byref(lk), 20e9, 0, 0, x, y, n, 1, None)
+
+
+@pytest.mark.parametrize("fn, n, needle", [
+    ("ssm_forward", 3072, "power of two"),   # the fused kernel needs 2^k
+    ("ssm_forward", 256, "power of two"),
+    ("ssm_cufft", 1, "[2, 2^27]"),          # the library-FFT path takes any length
+    ("ssm_cufft", (1 << 27) + 1, "[2, 2^27]"),
+])
+def test_split_step_length_checks(L, fn, n, needle):
+    assert _split_step(L, fn, n) == -1
+    assert needle in L.ldbp_last_error().decode()
+
+
+@pytest.mark.parametrize("kw, code, needle", [
+    (dict(link=dict(n_spans=0)), -1, "n_spans >= 1"),
+    (dict(fiber=dict(alpha_db_per_km=-0.1)), -1, "alpha"),
+    (dict(fiber=dict(gamma_per_w_km=float("nan"))), -6, "NaN"),
+])
+def test_split_step_parameter_checks(L, kw, code, needle):
+    for fn in ("ssm_forward", "ssm_cufft"):
+        assert _split_step(L, fn, 4096, **dict(kw)) == code
+        assert needle in L.ldbp_last_error().decode()
