@@ -123,3 +123,10 @@ def test_training_log_record():
     rec = train.iteration_record(7, 1e-2, 5e-4, [9, 7, 5])
     assert rec == {"step": 7, "loss": 1e-2, "snr_db": 20.0, "lr": 5e-4, "taps": 21, "T": [9, 7, 5]}
     assert json.loads(json.dumps(rec)) == rec
+
+
+def test_receiver_chain_runs_rx_on_the_served_output():
+    r, be = _receiver(25.9, 25.7)
+    assert r("y", "s", 1e-3) == ("dbp", None)  # before validation: DBP
+    r.validate("y", "s", 1e-3)
+    assert r("y", "s", 1e-3) == ("ldbp", None)
