@@ -119,3 +119,28 @@ def test_interpolation_round_trip_and_errors():
         txrx.lowpass_sample(up, n_d, 1.5)
     with pytest.raises(ValueError):
         txrx.interpolate(x, 100)
+
+
+def test_wdm_channel_selection_at_37p5_ghz():
+    # The 32 GBd WDM case of Sec. V: rho_a = 10 (Table I), channels on a 50 GHz
+    # grid, Delta B = 37.5 GHz at f_s = 64 GHz.  Read two-sided (|f| < 18.75 GHz)
+    # the front end returns exactly the centre channel sampled at rho_d = 2: its
+    # RRC band |f| <= 17.6 GHz passes and the neighbours (32.4..67.6 GHz off
+    # centre) are rejected.  Read one-sided (|f| < 37.5 GHz) the neighbours'
+    # inner edges (32.4..37.5 GHz) would pass and fold back into the band when
+    # sampled at f_s = 64 GHz.
+    nsym, Rs, rho_a, rho_d, P = 256, 32e9, 10, 2, 1e-3
+    n_a, n_d = nsym * rho_a, nsym * rho_d
+    t = np.arange(n_a) / (rho_a * Rs)
+    s = synth.qam16_symbols(3, nsym, seed=17)
+    centre = txrx.tx(s[0], rho_a, 0.1, P)
+    wdm = centre + sum(txrx.tx(s[i], rho_a, 0.1, P) * np.exp(2j * np.pi * f * t)
+                       for i, f in ((1, -50e9), (2, 50e9)))
+    bw = 37.5e9 / (rho_d * Rs)
+    out = txrx.lowpass_sample(wdm, n_d, bw)
+    ref = txrx.tx(s[0], rho_d, 0.1, P)
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(ref))
+    bin_hz = Rs / nsym
+    wide = np.fft.ifft(np.fft.fft(wdm, axis=-1) * txrx.brickwall_mask(n_a, 2 * 37.5e9 / bin_hz), axis=-1)
+    one_sided = wide[:, :: rho_a // rho_d]
+    assert np.max(np.abs(one_sided - ref)) > 1e-2 * np.max(np.abs(ref))
