@@ -1,6 +1,7 @@
 // Shared device/host helpers of the GB300 split-step library (sm_103a only).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +33,19 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// a * (h + l): product with a constant held as a float head h and a small
+// tail l; the tail enters below the rounding of the head products.
+__device__ __forceinline__ float2 cmul_hl(float2 a, float2 h, float2 l) {
+  return make_float2(fmaf(a.x, h.x, fmaf(-a.y, h.y, fmaf(a.x, l.x, -a.y * l.y))),
+                     fmaf(a.x, h.y, fmaf(a.y, h.x, fmaf(a.x, l.y, a.y * l.x))));
+}
+// Tail stored as half2 bits in units of `scale`.
+__device__ __forceinline__ float2 tail_h2(uint32_t bits, float scale) {
+  __half2 q;
+  memcpy(&q, &bits, sizeof(q));
+  const float2 f = __half22float2(q);
+  return make_float2(f.x * scale, f.y * scale);
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

@@ -17,14 +17,15 @@
 
 namespace ldbp {
 
-__global__ void spectral_kernel(float2* __restrict__ X, const float2* __restrict__ tab, float scale,
+__global__ void spectral_kernel(float2* __restrict__ X, const float2* __restrict__ tab,
+                                const uint32_t* __restrict__ tab_lo, float lo_scale, float scale,
                                 const float2* __restrict__ ntab, int noise, float noise_std, float flat, int span,
                                 uint32_t counter, uint32_t seed_lo, uint32_t seed_hi, long long n, long long total) {
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < total;
        m += (long long)gridDim.x * blockDim.x) {
     const long long b = m / n, k = m - b * n;
-    const float2 h = tab[k];
-    float2 A = cmul(X[m], make_float2(h.x * scale, h.y * scale));
+    float2 A = cmul_hl(X[m], tab[k], tail_h2(tab_lo[k], lo_scale));
+    A = make_float2(A.x * scale, A.y * scale);
     if (noise) {
       const float2 g = ase_normal((uint32_t)k, (uint32_t)b, (uint32_t)span, counter, seed_lo, seed_hi);
       const float2 hn = ntab ? ntab[k] : make_float2(flat, 0.f);
@@ -91,7 +92,8 @@ extern "C" int ssm_cufft(const ldbp_fiber* fiber, const ldbp_link* link, double 
   for (const SsmStep& s : dp->host_steps) {
     if (cufftExecC2C(plan, (cufftComplex*)Y, (cufftComplex*)Y, CUFFT_FORWARD) != CUFFT_SUCCESS)
       return fail(LDBP_ECUDA, "cufftExecC2C forward failed");
-    spectral_kernel<<<blocks, 256, 0, st>>>(Y, dp->tabs[s.tab], s.scale, s.noise_tab >= 0 ? dp->tabs[s.noise_tab] : nullptr,
+    spectral_kernel<<<blocks, 256, 0, st>>>(Y, dp->tabs[s.tab], dp->tabs_lo[s.tab], dp->tabs_lo_scale[s.tab], s.scale,
+                                            s.noise_tab >= 0 ? dp->tabs[s.noise_tab] : nullptr,
                                             s.noise_tab > -2, dp->noise_std, 1.0f / (float)n, s.span,
                                             (uint32_t)ctr, (uint32_t)seed, (uint32_t)(seed >> 32), n, total);
     if (cufftExecC2C(plan, (cufftComplex*)Y, (cufftComplex*)Y, CUFFT_INVERSE) != CUFFT_SUCCESS)

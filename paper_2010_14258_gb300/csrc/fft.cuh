@@ -12,24 +12,44 @@
 
 namespace ldbp {
 
+// cos and sin of 2 pi / 16 and 2 pi * 2 / 16, each split into a float head and
+// the float rounding of its remainder (head + tail carries about 48 bits).
+// The tails matter: the split-step kernel applies the same transform
+// thousands of times, and a constant whose float rounding has |w| != 1
+// scales every sample passing through it by the same factor each time.
+constexpr double kC1d = 0.92387953251128675613, kS1d = 0.38268343236508977173, kR2d = 0.70710678118654752440;
+constexpr float kC1h = (float)kC1d, kC1l = (float)(kC1d - (double)kC1h);
+constexpr float kS1h = (float)kS1d, kS1l = (float)(kS1d - (double)kS1h);
+constexpr float kR2h = (float)kR2d, kR2l = (float)(kR2d - (double)kR2h);
+
+// c * s for a head/tail constant (c = ch + cl): one rounding of the sum.
+__device__ __forceinline__ float mul_hl(float ch, float cl, float v) { return fmaf(ch, v, cl * v); }
+// a * c + b * s for head/tail constants c and s.
+__device__ __forceinline__ float dot_hl(float a, float ch, float cl, float b, float sh, float sl) {
+  return fmaf(a, ch, fmaf(b, sh, fmaf(a, cl, b * sl)));
+}
+
 // exp(-j 2 pi e / 16) applied to v; e is a compile-time constant.
 template <int e>
 __device__ __forceinline__ float2 tw16(float2 v) {
   constexpr int m = e & 15;
-  constexpr float C1 = 0.923879532511286756f, S1 = 0.382683432365089772f, R2 = 0.707106781186547524f;
   if constexpr (m == 0) return v;
   else if constexpr (m == 4) return make_float2(v.y, -v.x);                 // -j
   else if constexpr (m == 8) return make_float2(-v.x, -v.y);                // -1
   else if constexpr (m == 12) return make_float2(-v.y, v.x);                // +j
-  else if constexpr (m == 2) return make_float2(R2 * (v.x + v.y), R2 * (v.y - v.x));
-  else if constexpr (m == 6) return make_float2(R2 * (v.y - v.x), -R2 * (v.x + v.y));
-  else if constexpr (m == 10) return make_float2(-R2 * (v.x + v.y), R2 * (v.x - v.y));
-  else if constexpr (m == 14) return make_float2(R2 * (v.x - v.y), R2 * (v.x + v.y));
+  else if constexpr (m == 2) return make_float2(mul_hl(kR2h, kR2l, v.x + v.y), mul_hl(kR2h, kR2l, v.y - v.x));
+  else if constexpr (m == 6) return make_float2(mul_hl(kR2h, kR2l, v.y - v.x), -mul_hl(kR2h, kR2l, v.x + v.y));
+  else if constexpr (m == 10) return make_float2(-mul_hl(kR2h, kR2l, v.x + v.y), mul_hl(kR2h, kR2l, v.x - v.y));
+  else if constexpr (m == 14) return make_float2(mul_hl(kR2h, kR2l, v.x - v.y), mul_hl(kR2h, kR2l, v.x + v.y));
   else {
-    // general: (c, -s) with c = cos(2 pi m / 16), s = sin(2 pi m / 16)
-    constexpr float c = (m == 1 || m == 15) ? C1 : (m == 3 || m == 13) ? S1 : (m == 5 || m == 11) ? -S1 : -C1;
-    constexpr float s = (m == 1 || m == 7) ? S1 : (m == 3 || m == 5) ? C1 : (m == 9 || m == 15) ? -S1 : -C1;
-    return make_float2(fmaf(v.x, c, v.y * s), fmaf(v.y, c, -v.x * s));
+    // general: v (c - j s) with c = cos(2 pi m / 16), s = sin(2 pi m / 16),
+    // both +-cos(pi/8) or +-sin(pi/8) in head/tail form
+    constexpr bool c_is_c1 = (m == 1 || m == 15 || m == 7 || m == 9);
+    constexpr float csg = (m == 1 || m == 15 || m == 3 || m == 13) ? 1.f : -1.f;
+    constexpr float ssg = (m <= 7) ? 1.f : -1.f;
+    constexpr float ch = csg * (c_is_c1 ? kC1h : kS1h), cl = csg * (c_is_c1 ? kC1l : kS1l);
+    constexpr float sh = ssg * (c_is_c1 ? kS1h : kC1h), sl = ssg * (c_is_c1 ? kS1l : kC1l);
+    return make_float2(dot_hl(v.x, ch, cl, v.y, sh, sl), dot_hl(v.y, ch, cl, -v.x, sh, sl));
   }
 }
 

@@ -9,6 +9,8 @@ namespace ldbp {
 // One split-step "program step": spectral multiply (and optional ASE add),
 // inverse transform, Kerr rotation.  In the spectral domain
 //   X' = scale * tab[k] * X + [noise] noise_tab[k] * noise_std * g_k(span)
+// where each table value is a float head (tabs) plus a tail (tabs_lo: the
+// remainder as a half2, in units of tabs_lo_scale)
 // (noise_tab == -1 means a flat 1/n), then u = iDFT(X') (1/n folded into the
 // tables) and u <- u exp(j c |u|^2) when c != 0.
 struct SsmStep {
@@ -28,7 +30,9 @@ struct SsmParams {
   int batch;
   int nsteps;
   const SsmStep* steps;                 // device [nsteps]
-  const float2* tabs[kSsmMaxTabs];      // device [n] each, DFT order
+  const float2* tabs[kSsmMaxTabs];      // device [n] each, DFT order: float head of each value
+  const uint32_t* tabs_lo[kSsmMaxTabs]; // device [n] each: tail (value - head) / tabs_lo_scale as half2 bits
+  float tabs_lo_scale[kSsmMaxTabs];
   const float2* twiddle;                // device twiddle buffer (layout in ssm_kernel.cuh)
   const float* wave_scale;              // device [batch] per-waveform factor of step 0, or nullptr
   int wave_mode;                        // factor = w, sqrt(w) or 1/sqrt(w) for mode 0, 1, 2

@@ -1,6 +1,7 @@
 // Host side of the split-step path: FP64 construction of the per-step spectral
-// tables of the channel and of DBP, a per-device cache of those tables, and
-// the C ABI entry points ssm_forward / dbp_apply.
+// tables of the channel and of DBP (stored as head/tail float pairs), the
+// unit-modulus twiddle tables of the cluster transform, a per-device cache of
+// both, and the C ABI entry points ssm_forward / dbp_apply.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -9,6 +10,10 @@
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <cuda_fp16.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "ssm.cuh"
@@ -119,12 +124,76 @@ static std::mutex g_cache_mu;
 static std::map<std::string, std::shared_ptr<DeviceProgram>> g_programs;
 static std::map<std::string, float2*> g_twiddles;
 
-static cudaError_t upload_c64(const std::vector<std::complex<double>>& v, float2** out) {
-  std::vector<float2> h(v.size());
-  for (size_t i = 0; i < v.size(); ++i) h[i] = make_float2((float)v[i].real(), (float)v[i].imag());
-  cudaError_t e = cudaMalloc(out, h.size() * sizeof(float2));
+template <typename T>
+static cudaError_t upload(const std::vector<T>& h, T** out) {
+  cudaError_t e = cudaMalloc(out, h.size() * sizeof(T));
   if (e != cudaSuccess) return e;
-  return cudaMemcpy(*out, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  return cudaMemcpy(*out, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Spectral table as a float head per value (the float rounding of each part)
+// and a tail: the remainder value - head divided by `scale` (the largest
+// remainder of the table) as a half2.  Head plus tail carry about 36 bits;
+// the split-step kernel multiplies by the same table at every step, so the
+// head's rounding alone would add up coherently over a long run.
+static cudaError_t upload_table(const std::vector<std::complex<double>>& v, float2** head, uint32_t** tail,
+                                float* scale) {
+  std::vector<float2> h(v.size());
+  std::vector<double> lo(2 * v.size());
+  double m = 0.0;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const double re = v[i].real(), im = v[i].imag();
+    h[i] = make_float2((float)re, (float)im);
+    lo[2 * i] = re - (double)h[i].x;
+    lo[2 * i + 1] = im - (double)h[i].y;
+    m = std::max(m, std::max(std::fabs(lo[2 * i]), std::fabs(lo[2 * i + 1])));
+  }
+  *scale = m > 0.0 ? (float)m : 1.0f;
+  std::vector<uint32_t> t(v.size());
+  for (size_t i = 0; i < v.size(); ++i) {
+    const __half2 q = __floats2half2_rn((float)(lo[2 * i] / *scale), (float)(lo[2 * i + 1] / *scale));
+    memcpy(&t[i], &q, sizeof(uint32_t));
+  }
+  cudaError_t e = upload(h, head);
+  if (e != cudaSuccess) return e;
+  return upload(t, tail);
+}
+
+// A float pair (c, s) close to (cos t, sin t) = w with c^2 + s^2 as close to 1
+// as the float grid allows near w.  Candidates: one part moved by up to
+// kUnitSteps float steps from its rounding, the other the float rounding of
+// sqrt(1 - part^2) or a neighbour of it; the pair with the smallest
+// |c^2 + s^2 - 1| (evaluated exactly in double) within kUnitMaxDist of w wins,
+// the plain rounding when nothing beats it.  A twiddle of modulus 1 applied
+// forward and its conjugate applied in the inverse transform cancel exactly,
+// so its angle error does not build up over the steps of a long run.
+static float2 unit_float2(double c, double s) {
+  constexpr int kUnitSteps = 8;
+  constexpr double kUnitMaxDist = 2e-6;
+  float2 best = make_float2((float)c, (float)s);
+  auto res = [](float x, float y) { return std::fabs((double)x * x + (double)y * y - 1.0); };
+  double bres = res(best.x, best.y);
+  for (int role = 0; role < 2; ++role) {
+    const double a_true = role == 0 ? c : s, o_true = role == 0 ? s : c;
+    float a = (float)a_true;
+    for (int k = 0; k < kUnitSteps; ++k) a = std::nextafter(a, -2.0f);
+    for (int k = -kUnitSteps; k <= kUnitSteps; ++k, a = std::nextafter(a, 2.0f)) {
+      const double rem = 1.0 - (double)a * (double)a;
+      if (rem < 0.0) continue;
+      const float o0 = (float)std::copysign(std::sqrt(rem), o_true);
+      const float cand[3] = {std::nextafter(o0, -2.0f), o0, std::nextafter(o0, 2.0f)};
+      for (float o : cand) {
+        const float x = role == 0 ? a : o, y = role == 0 ? o : a;
+        const double dist = std::hypot((double)x - c, (double)y - s);
+        const double r = res(x, y);
+        if (dist <= kUnitMaxDist && r < bres) {
+          best = make_float2(x, y);
+          bres = r;
+        }
+      }
+    }
+  }
+  return best;
 }
 
 int get_twiddle(long long n, int P, int log_n2, float2** out) {
@@ -154,8 +223,10 @@ int get_twiddle(long long n, int P, int log_n2, float2** out) {
     }
     logns += logr;
   }
+  std::vector<float2> wf(w.size());
+  for (size_t i = 0; i < w.size(); ++i) wf[i] = unit_float2(w[i].real(), w[i].imag());
   float2* d = nullptr;
-  cudaError_t e = upload_c64(w, &d);
+  cudaError_t e = upload(wf, &d);
   if (e != cudaSuccess) return cuda_fail(e, "twiddle table");
   g_twiddles[key] = d;
   *out = d;
@@ -175,9 +246,13 @@ int get_program(const std::string& key_in, const SsmProgram& prog, std::shared_p
   auto dp = std::make_shared<DeviceProgram>();
   for (const auto& t : prog.tabs) {
     float2* d = nullptr;
-    cudaError_t e = upload_c64(t, &d);
+    uint32_t* dl = nullptr;
+    float sc = 1.f;
+    cudaError_t e = upload_table(t, &d, &dl, &sc);
     if (e != cudaSuccess) return cuda_fail(e, "ssm table");
     dp->tabs.push_back(d);
+    dp->tabs_lo.push_back(dl);
+    dp->tabs_lo_scale.push_back(sc);
   }
   cudaError_t e = cudaMalloc(&dp->steps, prog.steps.size() * sizeof(SsmStep));
   if (e != cudaSuccess) return cuda_fail(e, "ssm steps");
@@ -238,7 +313,11 @@ int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, in
   p.batch = batch;
   p.nsteps = dp.nsteps;
   p.steps = dp.steps;
-  for (size_t i = 0; i < dp.tabs.size() && i < (size_t)kSsmMaxTabs; ++i) p.tabs[i] = dp.tabs[i];
+  for (size_t i = 0; i < dp.tabs.size() && i < (size_t)kSsmMaxTabs; ++i) {
+    p.tabs[i] = dp.tabs[i];
+    p.tabs_lo[i] = dp.tabs_lo[i];
+    p.tabs_lo_scale[i] = dp.tabs_lo_scale[i];
+  }
   p.twiddle = tw;
   p.wave_scale = wave_scale;
   p.wave_mode = wave_mode;

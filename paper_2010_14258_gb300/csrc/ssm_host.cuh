@@ -31,7 +31,9 @@ SsmProgram build_dbp(const ldbp_fiber& f, const ldbp_link& l, double fs, long lo
                      bool symmetric);
 
 struct DeviceProgram {
-  std::vector<float2*> tabs;
+  std::vector<float2*> tabs;        // float heads, [n] each
+  std::vector<uint32_t*> tabs_lo;   // tails as half2 bits in units of tabs_lo_scale, [n] each
+  std::vector<float> tabs_lo_scale;
   std::vector<SsmStep> host_steps;
   SsmStep* steps = nullptr;
   int nsteps = 0;

@@ -16,9 +16,20 @@
 //      r -> X[k2 + N2 k1], applies the step's spectral multiply (and noise),
 //      conjugates, runs the P-point DFT again, multiplies by the same twiddles
 //      and pushes the value for r back to block r;
-//   3. local N2-point FFT of the conjugated data; conjugating its output gives
-//      the inverse transform, and the Kerr rotation is applied in registers
-//      before the result is stored.
+//   3. local N2-point transform of the conjugated data with the passes of
+//      step 1 transposed and in reverse order (decimation in frequency);
+//      conjugating its output gives the inverse transform, and the Kerr
+//      rotation is applied in registers before the result is stored.
+//
+// Accuracy over thousands of steps.  The inverse is the exact algebraic
+// inverse of the forward transform built from the same rounded constants:
+// every pass of step 3 is the transpose of a pass of step 1, the twiddle
+// tables hold float pairs with |w|^2 = 1 to about 1e-9 (chosen on the host),
+// and the radix-8/16 constants carry a tail term.  Then a constant's angle
+// error cancels between the two transforms instead of adding up step after
+// step, and no constant scales a sample path by |w| != 1.  The spectral
+// tables hold a head and a tail float per value for the same reason: the
+// same table multiplies the spectrum at every step.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -48,8 +59,9 @@ __host__ __device__ constexpr int ssm_stage_offset(int logn2, int logns_target) 
   return off;
 }
 
-// One radix-R Stockham pass of the local N2-point forward FFT (in place,
-// loads complete before stores).  Ns = product of the earlier radices.
+// One radix-R Stockham pass of the local N2-point forward FFT (decimation in
+// time; in place, loads complete before stores).  Ns = product of the
+// earlier radices.
 // PUSH_P > 1 (last pass of the forward transform in a P-block cluster): the
 // outputs go straight to their owners' receive buffers (st.async counted on
 // the owner's bars[0]) instead of local shared memory: output k2 belongs to
@@ -59,8 +71,8 @@ struct SsmPush {
   int r;
 };
 
-template <int LOGN2, int LOGNS, int LOGR, bool LAST_OF_INVERSE, int PUSH_P = 0>
-__device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict__ stw, float c,
+template <int LOGN2, int LOGNS, int LOGR, int PUSH_P = 0>
+__device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict__ stw,
                                          const SsmPush& push = SsmPush{0u, 0u, 0}) {
   constexpr int N2 = 1 << LOGN2, R = 1 << LOGR, Ns = 1 << LOGNS, NT = N2 / kSsmE, NB = kSsmE / R;
   const float2* __restrict__ tw = stw + ssm_stage_offset(LOGN2, LOGNS);
@@ -82,14 +94,6 @@ __device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict_
       for (int q = 1; q < R; ++q) a[i * R + q] = cmul(a[i * R + q], tw[(q - 1) * Ns + k]);
     }
     dft<R>(&a[i * R]);
-    if constexpr (LAST_OF_INVERSE) {
-      // conjugation completes the inverse transform; then the Kerr step on
-      // the thread's 16 samples (the last pass is always radix 16)
-      static_assert(R == kSsmE && NB == 1, "last inverse pass holds all of the thread's samples");
-#pragma unroll
-      for (int q = 0; q < R; ++q) a[q] = make_float2(a[q].x, -a[q].y);
-      if (c != 0.f) tile_kerr<kSsmE>(a, c);
-    }
     const int base = (j - k) * R + k;
     if constexpr (PUSH_P > 1) {
       constexpr int C = N2 / PUSH_P;
@@ -107,14 +111,80 @@ __device__ __forceinline__ void ssm_pass(float2* sbuf, const float2* __restrict_
   __syncthreads();
 }
 
-template <int LOGN2, int LOGNS, bool INVERSE, int PUSH_P = 0>
-__device__ __forceinline__ void ssm_local_fft(float2* sbuf, const float2* stw, float c,
+// The transpose of ssm_pass (decimation in frequency): it reads where
+// ssm_pass writes, runs the same radix-R DFT (a symmetric matrix), applies
+// the twiddles after it and writes where ssm_pass reads.  With unit-modulus
+// twiddles, conj o (these passes in reverse order) o conj is the exact
+// inverse of the forward passes, up to the factor N2.
+// LAST (the pass with Ns = 1, run last): the conjugation completes the
+// inverse, then the Kerr step on the thread's 16 samples.
+template <int LOGN2, int LOGNS, int LOGR, bool LAST>
+__device__ __forceinline__ void ssm_pass_dif(float2* sbuf, const float2* __restrict__ stw, float c) {
+  constexpr int N2 = 1 << LOGN2, R = 1 << LOGR, Ns = 1 << LOGNS, NT = N2 / kSsmE, NB = kSsmE / R;
+  const float2* __restrict__ tw = stw + ssm_stage_offset(LOGN2, LOGNS);
+  const int t = threadIdx.x;
+  float2 a[kSsmE];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = t + i * NT;
+    const int k = j & (Ns - 1);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) a[i * R + q] = sbuf[spad(base + q * Ns)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = t + i * NT;
+    const int k = j & (Ns - 1);
+    dft<R>(&a[i * R]);
+    if constexpr (Ns > 1) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) a[i * R + q] = cmul(a[i * R + q], tw[(q - 1) * Ns + k]);
+    }
+  }
+  if constexpr (LAST) {
+    static_assert(LOGNS == 0, "the last inverse pass is the one with Ns = 1");
+#pragma unroll
+    for (int q = 0; q < kSsmE; ++q) a[q] = make_float2(a[q].x, -a[q].y);
+    if (c != 0.f) tile_kerr<kSsmE>(a, c);
+  }
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    const int j = t + i * NT;
+#pragma unroll
+    for (int q = 0; q < R; ++q) sbuf[spad(j + q * (N2 / R))] = a[i * R + q];
+  }
+  __syncthreads();
+}
+
+// Pass list of the local transform: pass 0 has radix 2^(LOGN2 % 4) (16 when
+// LOGN2 % 4 == 0), every later pass radix 16.
+__host__ __device__ constexpr int ssm_first_logr(int logn2) { return (logn2 % 4) != 0 ? (logn2 % 4) : 4; }
+__host__ __device__ constexpr int ssm_pass_logns(int logn2, int idx) {
+  return idx == 0 ? 0 : ssm_first_logr(logn2) + 4 * (idx - 1);
+}
+__host__ __device__ constexpr int ssm_pass_logr(int logn2, int idx) { return idx == 0 ? ssm_first_logr(logn2) : 4; }
+__host__ __device__ constexpr int ssm_npass(int logn2) { return 1 + (logn2 - ssm_first_logr(logn2)) / 4; }
+
+// Forward local transform: passes 0 .. npass-1 (the last one may push).
+template <int LOGN2, int IDX, int PUSH_P = 0>
+__device__ __forceinline__ void ssm_local_fft(float2* sbuf, const float2* stw,
                                               const SsmPush& push = SsmPush{0u, 0u, 0}) {
-  if constexpr (LOGNS < LOGN2) {
-    constexpr int LOGR = (LOGNS == 0 && (LOGN2 % 4) != 0) ? (LOGN2 % 4) : 4;
-    constexpr bool last = LOGNS + LOGR == LOGN2;
-    ssm_pass<LOGN2, LOGNS, LOGR, INVERSE && last, (!INVERSE && last) ? PUSH_P : 0>(sbuf, stw, c, push);
-    ssm_local_fft<LOGN2, LOGNS + LOGR, INVERSE, PUSH_P>(sbuf, stw, c, push);
+  if constexpr (IDX < ssm_npass(LOGN2)) {
+    constexpr bool last = IDX + 1 == ssm_npass(LOGN2);
+    ssm_pass<LOGN2, ssm_pass_logns(LOGN2, IDX), ssm_pass_logr(LOGN2, IDX), last ? PUSH_P : 0>(sbuf, stw, push);
+    ssm_local_fft<LOGN2, IDX + 1, PUSH_P>(sbuf, stw, push);
+  }
+}
+
+// Inverse local transform (on conjugated data): the transposed passes
+// npass-1 .. 0, Kerr fused into pass 0.
+template <int LOGN2, int IDX>
+__device__ __forceinline__ void ssm_local_ifft(float2* sbuf, const float2* stw, float c) {
+  if constexpr (IDX >= 0) {
+    ssm_pass_dif<LOGN2, ssm_pass_logns(LOGN2, IDX), ssm_pass_logr(LOGN2, IDX), IDX == 0>(sbuf, stw, c);
+    ssm_local_ifft<LOGN2, IDX - 1>(sbuf, stw, c);
   }
 }
 
@@ -144,12 +214,18 @@ __device__ __forceinline__ bool ssm_middle(float2* sbuf, float2* recv, uint64_t*
   // frequencies are fetched from global memory first, so that their latency
   // overlaps the exchange below.
   const float2* __restrict__ H = p.tabs[st.tab];
+  const uint32_t* __restrict__ HL = p.tabs_lo[st.tab];
+  const float hl_scale = p.tabs_lo_scale[st.tab];
   float2 hv[NK][P], wv[NK][P > 1 ? P - 1 : 1];
+  uint32_t hl[NK][P];
 #pragma unroll
   for (int i = 0; i < NK; ++i) {
     const int k2 = r * C + t + i * NT;
 #pragma unroll
-    for (int k1 = 0; k1 < P; ++k1) hv[i][k1] = __ldg(&H[k2 + N2 * k1]);
+    for (int k1 = 0; k1 < P; ++k1) {
+      hv[i][k1] = __ldg(&H[k2 + N2 * k1]);
+      hl[i][k1] = __ldg(&HL[k2 + N2 * k1]);
+    }
 #pragma unroll
     for (int q = 1; q < P; ++q) wv[i][q - 1] = __ldg(&p.twiddle[(q - 1) * N2 + k2]);
   }
@@ -184,8 +260,8 @@ __device__ __forceinline__ bool ssm_middle(float2* sbuf, float2* recv, uint64_t*
 #pragma unroll
     for (int k1 = 0; k1 < P; ++k1) {
       const int k = k2 + N2 * k1;
-      const float2 h = hv[i][k1];
-      float2 A = cmul(a[k1], make_float2(h.x * sc, h.y * sc));
+      float2 A = cmul_hl(a[k1], hv[i][k1], tail_h2(hl[i][k1], hl_scale));
+      A = make_float2(A.x * sc, A.y * sc);
       if (noise) {
         const float2 g = ase_normal((uint32_t)k, (uint32_t)b, (uint32_t)st.span, p.counter, p.seed_lo, p.seed_hi);
         const float2 hn = HN ? __ldg(&HN[k]) : make_float2(flat, 0.f);
@@ -246,9 +322,9 @@ __global__ void __launch_bounds__((1 << LOGN2) / kSsmE, (512 / ((1 << LOGN2) / k
   const SsmPush push{smem_u32(recv), smem_u32(&bars[0]), r};
   for (int s = 0; s < p.nsteps; ++s) {
     const SsmStep st = p.steps[s];
-    ssm_local_fft<LOGN2, 0, false, P>(sbuf, stw, 0.f, push);
+    ssm_local_fft<LOGN2, 0, P>(sbuf, stw, push);
     if (!ssm_middle<LOGN2, P>(sbuf, recv, bars, (uint32_t)(s & 1), r, b, st, p, s == 0)) stop = 1;
-    ssm_local_fft<LOGN2, 0, true>(sbuf, stw, st.c);  // its barriers make `stop` visible
+    ssm_local_ifft<LOGN2, ssm_npass(LOGN2) - 1>(sbuf, stw, st.c);  // its barriers make `stop` visible
     if (stop) break;
   }
   cluster_barrier<P>(cl);  // no block leaves while a peer may still store into it

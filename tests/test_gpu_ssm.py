@@ -137,10 +137,11 @@ def test_full_size_dbp_sampled():
 ])
 def test_full_size_channel_sampled(B, n, fs, spans, span_km, stps, sps):
     # full-size channel runs with ASE: a sampled waveform vs the oracle (same
-    # Philox noise).  The FP32 error of a split-step run grows linearly with
-    # the step count (the rounded twiddles and spectral tables act the same
-    # way every step): allow 4e-7 per step (about 3 FP32 ulps), and require the
-    # fused kernel to be within 2x of the cuFFT evaluation of the same program.
+    # Philox noise), at the stated tolerance of 1e-4 after all steps.  Over
+    # 2000-2500 steps this needs the inverse transform to be the exact inverse
+    # of the forward one (unit-modulus twiddles, transposed passes) and the
+    # spectral tables in head + tail form; the library-FFT evaluation of the
+    # same program, which has neither, is printed for comparison.
     import torch
     from paper_2010_14258_gb300 import api
     gpu_lib()
@@ -151,9 +152,8 @@ def test_full_size_channel_sampled(B, n, fs, spans, span_km, stps, sps):
     y = api.ssm_forward(fib, link, fs, xd)
     yc = api.ssm_cufft(fib, link, fs, xd[0:1].contiguous())
     torch.cuda.synchronize()
-    steps = spans * stps
     # waveform 0 (its ASE draws use waveform index 0, as in a one-waveform oracle run)
     ref = nlse.channel(x[0:1], fib, link, fs)
     err, err_cufft = rel_l2(to_np(y[0:1]), ref), rel_l2(to_np(yc), ref)
-    assert err <= 4e-7 * steps
-    assert err <= 2.0 * err_cufft + 1e-6
+    print(f"{spans * stps} steps: fused {err:.2e}, library FFT {err_cufft:.2e}")
+    assert err <= 1e-4
