@@ -59,6 +59,19 @@ int ldbp_version(void);
  * wait inside a kernel ran out since the last call, or LDBP_ECUDA. */
 int ldbp_device_status(void);
 
+/* ldbp_wait_probe -- exercises the bounded device wait of the library's
+ * kernels (failure detection; the paper has no counterpart).  One block
+ * initialises a shared-memory mbarrier that expects two arrivals, makes
+ * `arrivals` of them (0, 1 or 2; no asynchronous copy is involved) and waits
+ * for the phase with the same bounded wait the TMA and cluster-exchange
+ * waits use, giving up after `limit` polls.  With fewer than two arrivals
+ * the wait runs out: the kernel records LDBP_ETIMEOUT in the device status
+ * word (read and cleared by ldbp_device_status) and returns; the context
+ * stays usable.  Asynchronous on `stream`.
+ * Errors: LDBP_EINVAL for arrivals outside 0..2 or limit outside
+ * 1..2^20; LDBP_ECUDA if the launch fails. */
+int ldbp_wait_probe(int32_t arrivals, int32_t limit, void* stream);
+
 /*
  * ldbp_apply -- learned digital backpropagation, forward pass.
  *

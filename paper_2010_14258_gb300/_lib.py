@@ -36,6 +36,7 @@ _SIGNATURES = {
     "ldbp_last_error": (ctypes.c_char_p, []),
     "ldbp_version": (c_int, []),
     "ldbp_device_status": (c_int, []),
+    "ldbp_wait_probe": (c_int, [c_int32, c_int32, c_void_p]),
     "ssm_forward": (c_int, [ctypes.POINTER(LdbpFiber), ctypes.POINTER(LdbpLink), c_double, c_void_p, c_void_p,
                             c_int64, c_int32, c_void_p]),
     "dbp_apply": (c_int, [ctypes.POINTER(LdbpFiber), ctypes.POINTER(LdbpLink), c_double, c_int32, c_int32,

@@ -77,11 +77,33 @@ static int check_model(const void* taps, int32_t taps_stride, const int32_t* T, 
   return 0;
 }
 
+// One mbarrier expecting two arrivals, `arrivals` of them made, then the
+// library's bounded wait on the phase (see ldbp_wait_probe).
+__global__ void wait_probe_kernel(int arrivals, int limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x < arrivals) mbar_arrive(&bar);
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, limit);
+}
+
 }  // namespace ldbp
 
 using namespace ldbp;
 
 extern "C" {
+
+int ldbp_wait_probe(int32_t arrivals, int32_t limit, void* stream) {
+  if (arrivals < 0 || arrivals > 2) return fail(LDBP_EINVAL, "arrivals=%d outside 0..2", arrivals);
+  if (limit < 1 || limit > (1 << 20)) return fail(LDBP_EINVAL, "limit=%d outside 1..2^20", limit);
+  wait_probe_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(arrivals, limit);
+  LDBP_CUDA_TRY(cudaGetLastError());
+  return LDBP_OK;
+}
 
 const char* ldbp_last_error(void) { return t_last_error; }
 

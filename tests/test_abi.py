@@ -167,3 +167,12 @@ def test_split_step_parameter_checks(L, kw, code, needle):
     for fn in ("ssm_forward", "ssm_cufft"):
         assert _split_step(L, fn, 4096, **dict(kw)) == code
         assert needle in L.ldbp_last_error().decode()
+
+
+def test_wait_probe_rejects_bad_arguments(L):
+    # host-side checks: nothing is launched
+    assert L.ldbp_wait_probe(3, 10, None) == -1
+    assert L.ldbp_wait_probe(-1, 10, None) == -1
+    assert L.ldbp_wait_probe(1, 0, None) == -1
+    assert L.ldbp_wait_probe(1, (1 << 20) + 1, None) == -1
+    assert b"limit" in L.ldbp_last_error()
