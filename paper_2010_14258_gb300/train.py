@@ -73,6 +73,21 @@ def iteration_record(step: int, loss: float, lr: float, T) -> dict:
             "taps": int(sum(T)), "T": [int(t) for t in T]}
 
 
+def prune_choice(taps, lengths, target: int) -> int:
+    """Which filter loses its outermost tap pair at a pruning step (Sec. IV-C):
+    among the filters still longer than `target`, the one whose outermost tap
+    h_K (K = (T - 1) / 2) has the smallest magnitude; ties go to the lowest
+    step index.  taps: [M, stride] half-tap vectors; returns -1 when every
+    filter is at its target."""
+    best, mag = -1, np.inf
+    for i, T in enumerate(lengths):
+        if T > target:
+            a = abs(taps[i][(T - 1) // 2])
+            if a < mag:
+                best, mag = i, a
+    return best
+
+
 def pruning_schedule(total_steps: int, iters: int, frac: float):
     """Front-loaded pruning iterations floor(frac iters (j/P)^2), j = 1..P."""
     return [int(math.floor(frac * iters * (j / total_steps) ** 2)) for j in range(1, total_steps + 1)]
@@ -208,13 +223,7 @@ class Trainer:
 
     def prune_one(self):
         """Remove the outermost tap pair of one filter (Sec. IV-C)."""
-        h = self.taps.cpu().numpy()
-        best, mag = -1, np.inf
-        for i, T in enumerate(self.T):
-            if T > self.cfg.t_end:
-                a = abs(h[i, (T - 1) // 2])
-                if a < mag:
-                    best, mag = i, a
+        best = prune_choice(self.taps.cpu().numpy(), self.T, self.cfg.t_end)
         if best >= 0:
             self.T[best] -= 2
 
