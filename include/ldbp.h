@@ -282,8 +282,12 @@ int ldbp_backward_workspace(int64_t n, int32_t batch, const int32_t* T, int32_t 
  *    LDBP_STATIC_SCRATCH_BYTES are rejected with LDBP_EINVAL and a message
  *    naming both sizes; nothing is launched.
  *  - The first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress (with that device current) and caches it; make that
- *    first call before any stream capture.  No call allocates or frees memory.
+ *    cudaGetSymbolAddress (with that device current) and caches it for the
+ *    current CUDA context; make that first call before any stream capture.
+ *    A device reset (cudaDeviceReset) destroys the context and the array may
+ *    be loaded elsewhere in the next one: the next call sees the new context
+ *    id and looks the address up again, so make it outside a capture too.
+ *    No call allocates or frees memory.
  *  - Every call on a device shares the one array and it keeps the last call's
  *    contents; nothing in it needs clearing, because each call writes every
  *    element it later reads.  Calls whose executions overlap on the GPU (on

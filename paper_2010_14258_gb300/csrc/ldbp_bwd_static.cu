@@ -1,6 +1,8 @@
 // ldbp_backward_static: the learned-DBP adjoint for callers that cannot
 // allocate device memory.  Its per-block tap sums go to a file-scope device
 // array instead of a caller-provided workspace.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -16,11 +18,48 @@ constexpr int kStaticMaxDevices = 64;
 static __device__ __align__(256) float2 g_bwd_scratch[kStaticScratchBytes / sizeof(float2)];
 
 static std::mutex g_static_mu;
-static void* g_static_addr[kStaticMaxDevices] = {};
 
-// Device address of g_bwd_scratch on the current device.  The host-side name
-// of the array is only a stand-in, so the address is looked up once per
-// device (with that device current) and cached.
+// The address is cached per CUDA context, keyed by the driver's unique
+// context id: a device reset destroys the primary context, the module is
+// loaded again in the next one and the array may move, so a cached address is
+// used only while the context it was looked up in is the current one.
+struct StaticAddr {
+  unsigned long long ctx_id;
+  void* addr;
+};
+static StaticAddr g_static_addr[kStaticMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Id of the context current on this thread (0 if none), through the
+// runtime's driver entry points (no link against the driver library).
+static int current_ctx_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return fail(LDBP_ECUDA, "driver entry point cuCtxGetCurrent unavailable");
+    get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return fail(LDBP_ECUDA, "driver entry point cuCtxGetId unavailable");
+    get_id = reinterpret_cast<CtxGetIdFn>(f);
+  }
+  CUcontext ctx = nullptr;
+  *id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS) return fail(LDBP_ECUDA, "cuCtxGetCurrent failed");
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return fail(LDBP_ECUDA, "cuCtxGetId failed");
+  return LDBP_OK;
+}
+
+// Device address of g_bwd_scratch in the current context.  The host-side
+// name of the array is only a stand-in, so the address is looked up with
+// cudaGetSymbolAddress (which also makes the device's primary context current
+// if none is) on the first call in a context and cached for that context.
 static int static_scratch(void** out) {
   int dev = 0;
   LDBP_CUDA_TRY(cudaGetDevice(&dev));
@@ -28,13 +67,16 @@ static int static_scratch(void** out) {
     return fail(LDBP_EUNSUPPORTED, "device %d beyond the %d devices the static scratch supports", dev,
                 kStaticMaxDevices);
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_addr[dev]) {
+  unsigned long long id = 0;
+  if (int rc = current_ctx_id(&id)) return rc;
+  if (id == 0 || !g_static_addr[dev].addr || g_static_addr[dev].ctx_id != id) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_bwd_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_bwd_scratch)");
-    g_static_addr[dev] = p;
+    if (int rc = current_ctx_id(&id)) return rc;
+    g_static_addr[dev] = StaticAddr{id, p};
   }
-  *out = g_static_addr[dev];
+  *out = g_static_addr[dev].addr;
   return LDBP_OK;
 }
 

@@ -66,9 +66,10 @@ def test_static_backward_rejects_problems_beyond_its_array():
     need = ctypes.c_size_t(0)
     _lib.check(_lib.lib().ldbp_backward_workspace(1 << 20, 64, _lib.i32_array(Ts), 25, ctypes.byref(need)))
     assert need.value > (4 << 20)
-    dummy = ctypes.c_void_p(256)  # never dereferenced: the size check rejects the call first
-    rc = _lib.lib().ldbp_backward_static(dummy, 16, _lib.i32_array(Ts), _lib.f32_array([0.0] * 25), 25, dummy,
-                                         dummy, None, dummy, 1 << 20, 64, None)
+    # NULL buffers: the size check rejects the call first; were that order ever
+    # changed, the NULL checks of ldbp_backward would reject it before any launch
+    rc = _lib.lib().ldbp_backward_static(None, 16, _lib.i32_array(Ts), _lib.f32_array([0.0] * 25), 25, None,
+                                         None, None, None, 1 << 20, 64, None)
     assert rc == -1
     msg = _lib.lib().ldbp_last_error().decode()
     assert "static array holds 4194304" in msg
