@@ -358,13 +358,15 @@ typedef struct {
  *  fs_hz         sampling rate of the waveform.
  *  x             device complex64 [batch][n] launch waveform in sqrt(W).
  *  y             device complex64 [batch][n]; may equal x (in place).
- *  n             power of two, 512 <= n <= 131072.
+ *  n             a power of two in 512..131072, or three times a power of two
+ *                in 1536..49152 (the 6 samples/symbol grids of the analog-rate
+ *                simulation: clusters of 3, 6 or 12 blocks).
  * One kernel launch runs all steps; each waveform stays in the shared memory
  * of a thread-block cluster.  The first call for a given (device, fiber,
  * link, fs, n) computes the FP64 spectral tables and uploads them into
  * library-owned device memory (cudaMalloc + synchronous copy); later calls
  * reuse them.
- * Errors: LDBP_EINVAL (NULL pointer, n not a supported power of two,
+ * Errors: LDBP_EINVAL (NULL pointer, n not a supported length,
  * non-positive fs/span/steps/batch, negative alpha); LDBP_ENONFINITE (a NaN
  * or infinite fiber, link or fs value); LDBP_ECUDA.
  */
@@ -454,21 +456,23 @@ int ldbp_rx(const void* y, const void* symbols, const float* power_w, int32_t sp
  * rejected.  With n_out > n_in the same formula is band-limited interpolation
  * onto a finer grid (e.g. a DSP-rate transmit waveform onto the analog grid).
  *  x          device complex64 [batch][n_in], 16-byte aligned
- *  y          device complex64 [batch][n_out] (output), 16-byte aligned; may
- *             alias x
- *  n_in, n_out  in [2, 2^27]; one divides the other
+ *  y          device complex64 [batch][n_out] (output), 16-byte aligned; it
+ *             may equal x when n_in == n_out and must not overlap it otherwise
+ *  n_in, n_out  one divides the other; the coarser one is a power of two in
+ *             512..4096, the ratio r = n_fine / n_coarse is at most 8 and
+ *             n_fine at most 16384 (e.g. 6144 -> 2048: 1024 symbols at
+ *             rho_a = 6 and rho_d = 2, the paper's frame, Table I)
  *  bandwidth  in (0, 1]
- *  workspace  device, >= ldbp_resample_workspace(n_in, batch) bytes, 16-byte
- *             aligned, overlapping neither x nor y; owned by the caller
- * Asynchronous on stream: a cuFFT forward transform (n_in), a passband gather
- * kernel, a cuFFT inverse transform (n_out).  cuFFT allocates its own work
- * area on the first call for a given (stream, n, batch).
+ * One kernel launch, asynchronous on stream: a block per waveform reads it
+ * once, runs r polyphase transforms of the coarse length (sampling down) or
+ * r inverse ones (interpolation) in shared memory, and writes the output
+ * once.  No workspace; the first call for a (device, n_coarse, r) uploads two
+ * small constant tables (cudaMalloc + synchronous copy).
  * Errors: LDBP_EINVAL (NULL pointer, sizes, misalignment, overlap, bandwidth
  * out of range), LDBP_ENONFINITE (bandwidth NaN or infinite), LDBP_ECUDA.
  */
-size_t ldbp_resample_workspace(int64_t n_in, int32_t batch);
 int ldbp_resample(const void* x, int64_t n_in, void* y, int64_t n_out, double bandwidth, int32_t batch,
-                  void* workspace, size_t workspace_bytes, void* stream);
+                  void* stream);
 
 /*
  * ldbp_ubench -- arithmetic ceilings of the current device (synchronous).

@@ -64,9 +64,7 @@ _SIGNATURES = {
     "ldbp_ragged_graph_capture": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ldbp_ragged_graph_launch": (c_int, [c_void_p, c_void_p]),
     "ldbp_ubench": (c_int, [c_int32, ctypes.POINTER(c_double)]),
-    "ldbp_resample_workspace": (ctypes.c_size_t, [c_int64, c_int32]),
-    "ldbp_resample": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_double, c_int32, c_void_p, ctypes.c_size_t,
-                              c_void_p]),
+    "ldbp_resample": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_double, c_int32, c_void_p]),
     "ldbp_apply": (c_int, [c_void_p, c_int32, P_int32, P_float, c_int32, c_void_p, c_void_p, c_int64, c_int32,
                            c_void_p, c_void_p]),
     "ldbp_apply_host_workspace": (ctypes.c_size_t, [c_int64, c_int32]),

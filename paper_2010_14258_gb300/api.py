@@ -186,7 +186,7 @@ def ssm_cufft(fiber, link, fs, x, dbp_steps_per_span=0, dbp_symmetric=False, out
     return y[0] if squeeze else y
 
 
-def resample(x, n_out, bandwidth=1.0, out=None, workspace=None):
+def resample(x, n_out, bandwidth=1.0, out=None):
     """Receiver front end of Sec. IV-A: brick-wall low-pass of bandwidth
     `bandwidth` x (the coarser grid's sample rate), sampled onto n_out points per
     waveform; with n_out > n_in, band-limited interpolation.  x: complex64 [B, n_in]."""
@@ -197,11 +197,7 @@ def resample(x, n_out, bandwidth=1.0, out=None, workspace=None):
     else:
         y = out.unsqueeze(0) if out.dim() == 1 else out
     _check_c64("out", y, (B, int(n_out)))
-    need = _lib.lib().ldbp_resample_workspace(n_in, B)
-    if workspace is None or workspace.numel() < need:
-        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=x2.device)
-    _lib.check(_lib.lib().ldbp_resample(_ptr(x2), n_in, _ptr(y), int(n_out), float(bandwidth), B, _ptr(workspace),
-                                        workspace.numel(), _stream()))
+    _lib.check(_lib.lib().ldbp_resample(_ptr(x2), n_in, _ptr(y), int(n_out), float(bandwidth), B, _stream()))
     return y[0] if squeeze else y
 
 

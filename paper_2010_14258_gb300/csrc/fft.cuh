@@ -1,4 +1,4 @@
-// Register-level DFT building blocks (radix 2, 4, 8, 16) and a shared-memory
+// Register-level DFT building blocks (radix 2, 3, 4, 6, 8, 12, 16) and a shared-memory
 // Stockham FFT for the cluster-resident split-step kernel.
 //
 // Convention: forward DFT X_k = sum_m x_m exp(-j 2 pi k m / N), natural order
@@ -21,6 +21,8 @@ constexpr double kC1d = 0.92387953251128675613, kS1d = 0.38268343236508977173, k
 constexpr float kC1h = (float)kC1d, kC1l = (float)(kC1d - (double)kC1h);
 constexpr float kS1h = (float)kS1d, kS1l = (float)(kS1d - (double)kS1h);
 constexpr float kR2h = (float)kR2d, kR2l = (float)(kR2d - (double)kR2h);
+constexpr double kS3d = 0.86602540378443864676;  // sqrt(3) / 2 = sin(2 pi / 6)
+constexpr float kS3h = (float)kS3d, kS3l = (float)(kS3d - (double)kS3h);
 
 // c * s for a head/tail constant (c = ch + cl): one rounding of the sum.
 __device__ __forceinline__ float mul_hl(float ch, float cl, float v) { return fmaf(ch, v, cl * v); }
@@ -75,11 +77,91 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
   a3 = psub(t1, t3);
 }
 
+// 3-point DFT on (a0, a1, a2), natural order:
+//   X0 = a0 + s,  X1,2 = a0 - s / 2 -+ j (sqrt(3) / 2) (a1 - a2),  s = a1 + a2.
+__device__ __forceinline__ void dft3(float2& a0, float2& a1, float2& a2) {
+  const float2 s = padd(a1, a2), d = psub(a1, a2);
+  const float2 t = __ffma2_rn(s, make_float2(-0.5f, -0.5f), a0);
+  // j sqrt(3)/2 d = (-sqrt(3)/2 d.y, sqrt(3)/2 d.x)
+  const float2 e = make_float2(-mul_hl(kS3h, kS3l, d.y), mul_hl(kS3h, kS3l, d.x));
+  a0 = padd(a0, s);
+  a1 = psub(t, e);
+  a2 = padd(t, e);
+}
+
+// exp(-j 2 pi e / 12) applied to v; e is a compile-time constant.  Every
+// value is built from 1/2 (exact) and sqrt(3)/2 (head + tail).
+template <int e>
+__device__ __forceinline__ float2 tw12(float2 v) {
+  constexpr int m = ((e % 12) + 12) % 12;
+  if constexpr (m == 0) return v;
+  else if constexpr (m == 3) return make_float2(v.y, -v.x);    // -j
+  else if constexpr (m == 6) return make_float2(-v.x, -v.y);   // -1
+  else if constexpr (m == 9) return make_float2(-v.y, v.x);    // +j
+  else {
+    // v (c - j s): c = cos(pi m / 6), s = sin(pi m / 6), each 0, +-1/2 or +-sqrt(3)/2
+    constexpr bool c_big = (m == 1 || m == 5 || m == 7 || m == 11);  // |c| = sqrt(3)/2, |s| = 1/2
+    constexpr float csg = (m == 1 || m == 2 || m == 10 || m == 11) ? 1.f : -1.f;
+    constexpr float ssg = (m < 6) ? 1.f : -1.f;
+    if constexpr (c_big) {
+      // x = c v.x + s v.y, y = c v.y - s v.x with |s| = 1/2 exact
+      return make_float2(fmaf(csg * kS3h, v.x, fmaf(csg * kS3l, v.x, 0.5f * ssg * v.y)),
+                         fmaf(csg * kS3h, v.y, fmaf(csg * kS3l, v.y, -0.5f * ssg * v.x)));
+    } else {
+      // |c| = 1/2 exact, |s| = sqrt(3)/2
+      return make_float2(fmaf(ssg * kS3h, v.y, fmaf(ssg * kS3l, v.y, 0.5f * csg * v.x)),
+                         fmaf(-ssg * kS3h, v.x, fmaf(-ssg * kS3l, v.x, 0.5f * csg * v.y)));
+    }
+  }
+}
+
 template <int R>
 __device__ __forceinline__ void dft(float2* a) {
   if constexpr (R == 1) {
   } else if constexpr (R == 2) {
     dft2(a[0], a[1]);
+  } else if constexpr (R == 3) {
+    dft3(a[0], a[1], a[2]);
+  } else if constexpr (R == 6) {
+    // R1 = 2, R2 = 3: b[m1][k2] = DFT3_{m2} a[m1 + 2 m2]; twiddle W6^{m1 k2} = W12^{2 m1 k2}; DFT2 over m1.
+    float2 b0[3] = {a[0], a[2], a[4]};
+    float2 b1[3] = {a[1], a[3], a[5]};
+    dft3(b0[0], b0[1], b0[2]);
+    dft3(b1[0], b1[1], b1[2]);
+    b1[1] = tw12<2>(b1[1]);
+    b1[2] = tw12<4>(b1[2]);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+      float2 x0 = b0[k2], x1 = b1[k2];
+      dft2(x0, x1);
+      a[k2] = x0;
+      a[k2 + 3] = x1;
+    }
+  } else if constexpr (R == 12) {
+    // R1 = 4, R2 = 3: b[m1][k2] = DFT3_{m2} a[m1 + 4 m2]; twiddle W12^{m1 k2}; DFT4 over m1.
+    float2 b[4][3];
+#pragma unroll
+    for (int m1 = 0; m1 < 4; ++m1) {
+      b[m1][0] = a[m1];
+      b[m1][1] = a[m1 + 4];
+      b[m1][2] = a[m1 + 8];
+      dft3(b[m1][0], b[m1][1], b[m1][2]);
+    }
+    b[1][1] = tw12<1>(b[1][1]);
+    b[1][2] = tw12<2>(b[1][2]);
+    b[2][1] = tw12<2>(b[2][1]);
+    b[2][2] = tw12<4>(b[2][2]);
+    b[3][1] = tw12<3>(b[3][1]);
+    b[3][2] = tw12<6>(b[3][2]);
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+      float2 x0 = b[0][k2], x1 = b[1][k2], x2 = b[2][k2], x3 = b[3][k2];
+      dft4(x0, x1, x2, x3);
+      a[k2] = x0;
+      a[k2 + 3] = x1;
+      a[k2 + 6] = x2;
+      a[k2 + 9] = x3;
+    }
   } else if constexpr (R == 4) {
     dft4(a[0], a[1], a[2], a[3]);
   } else if constexpr (R == 8) {

@@ -288,9 +288,13 @@ int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x
   if (batch < 1) return fail(LDBP_EINVAL, "batch=%d must be >= 1", batch);
   if (!pow2) {
     if (n < 2 || n > (1LL << 27)) return fail(LDBP_EINVAL, "n=%lld must be in [2, 2^27]", n);
-  } else if (n < (1LL << kSsmMinLogN2) || n > (1LL << (kSsmMaxLogN2 + 4)) || (n & (n - 1))) {
-    return fail(LDBP_EINVAL, "n=%lld must be a power of two in [%d, %d]", n, 1 << kSsmMinLogN2,
-                1 << (kSsmMaxLogN2 + 4));
+  } else {
+    const bool three = n % 3 == 0;
+    const long long m = three ? n / 3 : n;
+    const long long lo = three ? (1LL << 9) : (1LL << kSsmMinLogN2), hi = three ? (1LL << 14) : (1LL << (kSsmMaxLogN2 + 4));
+    if (m < lo || m > hi || (m & (m - 1)))
+      return fail(LDBP_EINVAL, "n=%lld must be a power of two in [%d, %d] or three times one in [%d, %d]", n,
+                  1 << kSsmMinLogN2, 1 << (kSsmMaxLogN2 + 4), 3 << 9, 3 << 14);
   }
   if ((long long)l->n_spans * l->steps_per_span > 1000000) return fail(LDBP_EINVAL, "too many steps");
   return 0;

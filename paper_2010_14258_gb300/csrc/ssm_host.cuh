@@ -44,8 +44,9 @@ int get_program(const std::string& key, const SsmProgram& prog, std::shared_ptr<
 // Cached program of the channel (dbp_steps == 0) or of DBP; tables built on a miss.
 int link_program(const ldbp_fiber& f, const ldbp_link& l, double fs, long long n, int dbp_steps, bool dbp_symmetric,
                  std::shared_ptr<DeviceProgram>* out);
-// Argument checks of the split-step entry points.  pow2: n must be a power of
-// two in the fused kernel's range; otherwise any n in [2, 2^27] (library FFT).
+// Argument checks of the split-step entry points.  pow2: n must be in the
+// fused kernel's range (2^9..2^17, or 3 * 2^9..3 * 2^14); otherwise any n in
+// [2, 2^27] (library FFT).
 int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x, const void* y, long long n,
                int batch, bool pow2 = true);
 int get_twiddle(long long n, int P, int log_n2, float2** out);

@@ -1,0 +1,9 @@
+// Instances of the split-step kernel with cluster size 12 (n = 3 * 2^k grids).
+#include "ssm_kernel.cuh"
+
+namespace ldbp {
+template cudaError_t launch_one<9, 12>(const SsmParams& p, cudaStream_t st);
+template cudaError_t launch_one<10, 12>(const SsmParams& p, cudaStream_t st);
+template cudaError_t launch_one<11, 12>(const SsmParams& p, cudaStream_t st);
+template cudaError_t launch_one<12, 12>(const SsmParams& p, cudaStream_t st);
+}  // namespace ldbp

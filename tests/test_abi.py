@@ -104,28 +104,23 @@ def test_ldbp_essm_apply_rejects(L, kw, needle):
 
 
 def _resample(L, **kw):
-    args = dict(x=ctypes.c_void_p(4096), n_in=384, y=ctypes.c_void_p(1 << 22), n_out=128, bw=1.0, B=2,
-                ws=ctypes.c_void_p(1 << 24), wsb=384 * 2 * 8)
+    args = dict(x=ctypes.c_void_p(4096), n_in=1536, y=ctypes.c_void_p(1 << 22), n_out=512, bw=1.0, B=2)
     args.update(kw)
-    return L.ldbp_resample(args["x"], args["n_in"], args["y"], args["n_out"], args["bw"], args["B"], args["ws"],
-                           args["wsb"], None)
-
-
-def test_resample_workspace_size(L):
-    assert L.ldbp_resample_workspace(384, 2) == 384 * 2 * 8
-    assert L.ldbp_resample_workspace(1, 2) == 0
+    return L.ldbp_resample(args["x"], args["n_in"], args["y"], args["n_out"], args["bw"], args["B"], None)
 
 
 @pytest.mark.parametrize("kw, needle", [
     (dict(x=None), "non-NULL"),
     (dict(bw=0.0), "bandwidth"),
     (dict(bw=1.5), "bandwidth"),
-    (dict(n_out=100), "divide"),
-    (dict(n_in=1), "n_in=1"),
+    (dict(n_out=500), "divide"),
+    (dict(n_in=999, n_out=333), "power of two"),       # odd coarse grid
+    (dict(n_in=768, n_out=256), "power of two"),        # coarse grid below 512
+    (dict(n_in=9 * 512, n_out=512), "ratio"),           # r = 9
+    (dict(n_in=8 * 4096, n_out=4096), "at most 16384"),  # fine grid too long
     (dict(B=0), "batch=0"),
-    (dict(wsb=100), "workspace"),
-    (dict(ws=ctypes.c_void_p((1 << 24) + 8)), "aligned"),
-    (dict(ws=ctypes.c_void_p(4096 + 64)), "overlaps"),
+    (dict(x=ctypes.c_void_p(4096 + 8)), "aligned"),
+    (dict(y=ctypes.c_void_p(4096 + 64)), "overlap"),
 ])
 def test_resample_rejects(L, kw, needle):
     assert _resample(L, **kw) == -1
@@ -148,8 +143,10 @@ def _split_step(L, fn, n, **kw):
 
 
 @pytest.mark.parametrize("fn, n, needle", [
-    ("ssm_forward", 3072, "power of two"),   # the fused kernel needs 2^k
+    ("ssm_forward", 5120, "power of two"),   # the fused kernel takes 2^k and 3 * 2^k only
     ("ssm_forward", 256, "power of two"),
+    ("ssm_forward", 768, "three times"),     # 3 * 2^8: below the 3 * 2^k range
+    ("ssm_forward", 3 << 15, "three times"),  # above it
     ("ssm_cufft", 1, "[2, 2^27]"),          # the library-FFT path takes any length
     ("ssm_cufft", (1 << 27) + 1, "[2, 2^27]"),
 ])

@@ -36,7 +36,12 @@ def _dbp(x, fiber, link, fs, N, sym):
 SHAPES = [(512, 3), (1024, 2), (4096, 1), (16384, 1), (65536, 2), (131072, 1), (32768, 64)]
 
 
-@pytest.mark.parametrize("n,B", SHAPES)
+# n = 3 * 2^k (6 samples/symbol grids): cluster sizes 3, 6 and 12 over
+# blocks of 512..4096 samples, uneven frequency chunks among the blocks
+SHAPES3 = [(1536, 1), (3072, 2), (6144, 1), (6144, 64), (12288, 64), (24576, 8), (49152, 4)]
+
+
+@pytest.mark.parametrize("n,B", SHAPES + SHAPES3)
 @pytest.mark.parametrize("symmetric", [True, False])
 def test_channel_parity_shapes(n, B, symmetric):
     fs = 20e9
@@ -70,12 +75,13 @@ def test_channel_with_ase_matches_philox_oracle():
         assert rel_l2(y, ref) <= 1e-4
 
 
+@pytest.mark.parametrize("n", [16384, 6144])
 @pytest.mark.parametrize("symmetric,N", [(True, 1), (False, 1), (True, 3), (False, 2)])
-def test_dbp_parity(symmetric, N):
+def test_dbp_parity(symmetric, N, n):
     fs = 20e9
     fib = synth.Fiber()
     link = synth.Link(4, 80.0, 5, True, False)
-    x = _sig(2, 16384, 3, 2e-3)
+    x = _sig(2, n, 3, 2e-3)
     y = nlse.channel(x, fib, link, fs)
     yc = c64(y)
     out = _dbp(yc, fib, link, fs, N, symmetric)

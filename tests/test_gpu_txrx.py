@@ -76,11 +76,11 @@ def test_cufft_path_matches_oracle(mode):
     assert rel_l2(to_np(out), ref) <= 1e-4
 
 
-@pytest.mark.parametrize("B,n_out,r,bw", [(3, 1024, 3, 1.0), (2, 1024, 3, 0.6), (1, 333, 3, 1.0), (2, 512, 4, 0.5),
-                                          (2, 256, 1, 0.8)])
+@pytest.mark.parametrize("B,n_out,r,bw", [(3, 1024, 3, 1.0), (2, 1024, 3, 0.6), (2, 2048, 3, 1.0), (1, 512, 5, 1.0),
+                                          (2, 512, 4, 0.5), (2, 512, 1, 0.8), (1, 4096, 4, 1.0), (2, 512, 8, 0.7)])
 def test_resample_down_matches_oracle(B, n_out, r, bw):
     # brick-wall low-pass + sampling at the DSP rate (Sec. IV-A), wideband input
-    # so that the filter cuts; odd grids and the plain low-pass (r = 1) included
+    # so that the filter cuts; the plain low-pass (r = 1) included
     import torch
     api = _api()
     x = c64(synth.gaussian_waveform(B, n_out * r, 40 + B, 1.0))
@@ -89,7 +89,7 @@ def test_resample_down_matches_oracle(B, n_out, r, bw):
     assert rel_l2(to_np(y), txrx.lowpass_sample(x, n_out, bw)) <= 2e-6
 
 
-@pytest.mark.parametrize("B,n_in,r", [(3, 1024, 3), (1, 333, 3), (2, 256, 8)])
+@pytest.mark.parametrize("B,n_in,r", [(3, 1024, 3), (2, 2048, 3), (1, 512, 7), (2, 512, 8), (1, 4096, 2)])
 def test_resample_up_matches_oracle(B, n_in, r):
     import torch
     api = _api()
@@ -99,12 +99,22 @@ def test_resample_up_matches_oracle(B, n_in, r):
     assert rel_l2(to_np(y), txrx.interpolate(x, n_in * r)) <= 2e-6
 
 
+def test_resample_in_place_low_pass():
+    import torch
+    api = _api()
+    x = c64(synth.gaussian_waveform(2, 1024, 57, 1.0))
+    xd = to_dev(x)
+    api.resample(xd, 1024, 0.5, out=xd)
+    torch.cuda.synchronize()
+    assert rel_l2(to_np(xd), txrx.lowpass_sample(x, 1024, 0.5)) <= 2e-6
+
+
 @pytest.mark.parametrize("symmetric,ase", [(True, True), (False, False)])
 def test_analog_rate_link_matches_oracle(symmetric, ase):
     # The system model of Sec. IV-A: transmit waveform on the analog grid
     # (rho_a = 6 samples/symbol, here interpolated from the DSP-rate transmitter),
-    # split-step channel on that non-power-of-two grid, brick-wall low-pass and
-    # sampling at rho_d = 2.  Oracle: the same chain in FP64 at rho_a.
+    # split-step channel on that 3 * 2^k grid (the fused cluster kernel), brick-wall
+    # low-pass and sampling at rho_d = 2.  Oracle: the same chain in FP64 at rho_a.
     import torch
     api = _api()
     B, nsym, rho_a, rho_d, Rs = 2, 512, 6, 2, 10e9
@@ -114,7 +124,7 @@ def test_analog_rate_link_matches_oracle(symmetric, ase):
     link = synth.Link(2, 80.0, 6, symmetric, ase, seed=9, counter=1)
     xd = api.tx(to_dev(s), torch.from_numpy(P).cuda(), sps=rho_d)
     xa = api.resample(xd, nsym * rho_a)
-    ya = api.ssm_cufft(fib, link, rho_a * Rs, xa)
+    ya = api.ssm_forward(fib, link, rho_a * Rs, xa)
     r = api.resample(ya, nsym * rho_d)
     torch.cuda.synchronize()
     ref = txrx.lowpass_sample(nlse.channel(txrx.tx(s, rho_a, 0.1, P.astype(np.float64)), fib, link, rho_a * Rs),
@@ -122,12 +132,38 @@ def test_analog_rate_link_matches_oracle(symmetric, ase):
     assert rel_l2(to_np(r), ref) <= 1e-4
 
 
-def test_resample_full_size_sampled_waveforms():
-    # 64 waveforms of 32768 symbols at rho_a = 6 (n = 196608) down to rho_d = 2
-    # and back up; waveforms 0 and 63 against the oracle.
+def test_analog_rate_link_full_size_sampled():
+    # the analog-rate workload: 2048 frames of the paper's 1024 symbols at
+    # rho_a = 6 (n = 6144), 25 x 80 km at 100 StPS with ASE on the fused kernel,
+    # then the front end down to rho_d = 2; frames 0 and 2047 against the oracle
     import torch
     api = _api()
-    B, nsym = 64, 32768
+    B, nsym, rho_a, rho_d, Rs = 2048, 1024, 6, 2, 10e9
+    s = synth.qam16_symbols(B, nsym, 71)
+    pw = np.full(B, 1.585e-3, np.float32)
+    fib = synth.Fiber()
+    link = synth.Link(25, 80.0, 100, True, True, seed=5, counter=3)
+    xa = api.resample(api.tx(to_dev(c64(s)), torch.from_numpy(pw).cuda(), sps=rho_d), nsym * rho_a)
+    ya = api.ssm_forward(fib, link, rho_a * Rs, xa)
+    r = api.resample(ya, nsym * rho_d)
+    torch.cuda.synchronize()
+    ch0 = nlse.channel(to_np(xa[0:1]), fib, link, rho_a * Rs)
+    assert rel_l2(to_np(ya[0:1]), ch0) <= 1e-4
+    assert rel_l2(to_np(r[0:1]), txrx.lowpass_sample(ch0, nsym * rho_d)) <= 1e-4
+    # the last frame alone with ASE off on both sides (a one-frame oracle run
+    # draws the noise of waveform index 0, not of index 2047)
+    link0 = synth.Link(25, 80.0, 100, True, False)
+    y0 = api.ssm_forward(fib, link0, rho_a * Rs, xa[B - 1:B].contiguous())
+    torch.cuda.synchronize()
+    assert rel_l2(to_np(y0), nlse.channel(to_np(xa[B - 1:B]), fib, link0, rho_a * Rs)) <= 1e-4
+
+
+def test_resample_full_size_sampled_waveforms():
+    # 2048 frames of 1024 symbols at rho_a = 6 (n = 6144) down to rho_d = 2 and
+    # back up; frames 0 and 2047 against the oracle.
+    import torch
+    api = _api()
+    B, nsym = 2048, 1024
     g = torch.Generator(device="cuda").manual_seed(61)
     x = torch.randn(B, 6 * nsym, dtype=torch.complex64, device="cuda", generator=g)
     y = api.resample(x, 2 * nsym)
