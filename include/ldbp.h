@@ -206,6 +206,11 @@ int ldbp_apply_host(const void* taps, int32_t taps_stride, const int32_t* T, con
  *     and replay it on `stream`.
  * ldbp_ragged_info         total samples, total steps, work items, tile cap,
  *     blocks per SM of the plan.
+ * ldbp_ragged_set_schedule pins the tile cap (even, 256..4096 output samples
+ *     per tile) and the blocks per SM (1..the occupancy of the plan's
+ *     K_max class), e.g. to replay a configuration the autotuner chose
+ *     earlier; rebuilds the work list (allocates; synchronous) and drops a
+ *     captured graph.
  * The plan is bound to the device current at creation.  Errors: LDBP_EINVAL
  * (NULL pointers, n < 1, M outside 1..LDBP_MAX_STEPS, T invalid, halo too
  * large, overlapping x / y, wrong device), LDBP_ECUDA.
@@ -216,6 +221,7 @@ int ldbp_ragged_plan_destroy(void* plan);
 int ldbp_ragged_info(const void* plan, int64_t* total_samples, int32_t* total_steps, int32_t* items,
                      int32_t* tile_cap, int32_t* blocks_per_sm);
 int ldbp_ragged_autotune(void* plan, const void* taps, const float* c, const void* x, void* y, void* stream);
+int ldbp_ragged_set_schedule(void* plan, int32_t tile_cap, int32_t blocks_per_sm);
 int ldbp_apply_ragged(void* plan, const void* taps, const float* c, const void* x, void* y, uint64_t* done_ns,
                       uint64_t* start_ns, void* stream);
 int ldbp_ragged_graph_capture(void* plan, const void* taps, const float* c, const void* x, void* y);

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "ldbp_ragged_plan_create": (c_int, [ctypes.POINTER(c_void_p), c_int32, ctypes.POINTER(c_int64), P_int32,
                                         P_int32, c_int32]),
     "ldbp_ragged_plan_destroy": (c_int, [c_void_p]),
+    "ldbp_ragged_set_schedule": (c_int, [c_void_p, c_int32, c_int32]),
     "ldbp_ragged_info": (c_int, [c_void_p, ctypes.POINTER(c_int64), P_int32, P_int32, P_int32, P_int32]),
     "ldbp_ragged_autotune": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ldbp_apply_ragged": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),

@@ -346,6 +346,10 @@ class RaggedPlan:
     def autotune(self, taps, c, x, y):
         _lib.check(_lib.lib().ldbp_ragged_autotune(self.handle, _ptr(taps), _ptr(c), _ptr(x), _ptr(y), _stream()))
 
+    def set_schedule(self, tile_cap, blocks_per_sm):
+        """Pin the tile cap and blocks per SM (e.g. a configuration autotuned earlier)."""
+        _lib.check(_lib.lib().ldbp_ragged_set_schedule(self.handle, int(tile_cap), int(blocks_per_sm)))
+
     def apply(self, taps, c, x, y, done_ns=None, start_ns=None):
         _lib.check(_lib.lib().ldbp_apply_ragged(self.handle, _ptr(taps), _ptr(c), _ptr(x), _ptr(y), _ptr(done_ns),
                                                 _ptr(start_ns), _stream()))

@@ -459,6 +459,27 @@ int ldbp_ragged_autotune(void* plan, const void* taps, const float* c, const voi
   return LDBP_OK;
 }
 
+int ldbp_ragged_set_schedule(void* plan, int32_t tile_cap, int32_t blocks_per_sm) {
+  if (!plan) return fail(LDBP_EINVAL, "plan must be non-NULL");
+  RaggedPlan* pl = static_cast<RaggedPlan*>(plan);
+  if (tile_cap < 256 || tile_cap > kFwdS || (tile_cap & 1))
+    return fail(LDBP_EINVAL, "tile_cap=%d must be even and in [256, %d]", tile_cap, kFwdS);
+  if (blocks_per_sm < 1 || blocks_per_sm > pl->max_blocks_per_sm)
+    return fail(LDBP_EINVAL, "blocks_per_sm=%d must be in [1, %d]", blocks_per_sm, pl->max_blocks_per_sm);
+  int dev = 0;
+  LDBP_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != pl->device) return fail(LDBP_EINVAL, "plan belongs to device %d, current is %d", pl->device, dev);
+  pl->tile_cap = tile_cap;
+  pl->grid_mult = blocks_per_sm;
+  cudaError_t e = ragged_build_items(*pl);
+  if (e != cudaSuccess) return cuda_fail(e, "ragged items");
+  if (pl->graph) {  // the captured graph refers to the old work list
+    cudaGraphExecDestroy(pl->graph);
+    pl->graph = nullptr;
+  }
+  return LDBP_OK;
+}
+
 int ldbp_ragged_graph_capture(void* plan, const void* taps, const float* c, const void* x, void* y) {
   if (!plan) return fail(LDBP_EINVAL, "plan must be non-NULL");
   RaggedPlan* pl = static_cast<RaggedPlan*>(plan);

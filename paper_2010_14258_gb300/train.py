@@ -44,6 +44,7 @@ class TrainConfig:
     powers_dbm: tuple = tuple(range(-4, 7))
     t_start: int = 31
     t_end: int = 3
+    t_end_odd: int = 0             # > 0: filters at odd step indices are pruned to this length (alternating, Sec. V-B)
     iters: int = 1000
     lr: float = 1e-3
     lr_final: float = 0.0          # cosine decay from lr to lr_final over the run (0: constant lr)
@@ -54,6 +55,7 @@ class TrainConfig:
     learn_c: bool = False          # train the nonlinear coefficients too (Remark 1)
     kappa: int = 0                 # > 0: learned enhanced SSM, a (2 kappa + 1)-tap filter on |v|^2 per step
     init: str = "ls"               # "ls", "unit" or "random" filters (Sec. V-E)
+    data_pool: int = 0             # > 0: make this many batches with the channel once and cycle through them
 
     @property
     def fs(self):
@@ -73,15 +75,17 @@ def iteration_record(step: int, loss: float, lr: float, T) -> dict:
             "taps": int(sum(T)), "T": [int(t) for t in T]}
 
 
-def prune_choice(taps, lengths, target: int) -> int:
+def prune_choice(taps, lengths, targets) -> int:
     """Which filter loses its outermost tap pair at a pruning step (Sec. IV-C):
-    among the filters still longer than `target`, the one whose outermost tap
-    h_K (K = (T - 1) / 2) has the smallest magnitude; ties go to the lowest
-    step index.  taps: [M, stride] half-tap vectors; returns -1 when every
-    filter is at its target."""
+    among the filters still longer than their target, the one whose outermost
+    tap h_K (K = (T - 1) / 2) has the smallest magnitude; ties go to the
+    lowest step index.  taps: [M, stride] half-tap vectors; targets: one
+    length for all filters or one per filter; returns -1 when every filter is
+    at its target."""
+    tg = [int(targets)] * len(lengths) if np.isscalar(targets) else [int(t) for t in targets]
     best, mag = -1, np.inf
     for i, T in enumerate(lengths):
-        if T > target:
+        if T > tg[i]:
             a = abs(taps[i][(T - 1) // 2])
             if a < mag:
                 best, mag = i, a
@@ -126,7 +130,8 @@ class Trainer:
         self.m = torch.zeros((M, self.stride, 2), dtype=torch.float32, device="cuda")
         self.v = torch.zeros_like(self.m)
         self.step_count = 0
-        steps = sum((cfg.t_start - cfg.t_end) // 2 for _ in range(M))
+        self.targets = [cfg.t_end_odd if (cfg.t_end_odd > 0 and i % 2 == 1) else cfg.t_end for i in range(M)]
+        steps = sum((cfg.t_start - t) // 2 for t in self.targets)
         self.schedule = pruning_schedule(steps, cfg.iters, cfg.prune_frac) if steps else []
         B, n = cfg.batch, cfg.n
         self.ckpt = torch.empty((M, B, n), dtype=torch.complex64, device="cuda")
@@ -134,6 +139,7 @@ class Trainer:
         self.ws_rx = torch.empty((B, n), dtype=torch.complex64, device="cuda")
         self.ws_bwd = None
         self.history = []
+        self.pool = [self._make_frames(it) for it in range(cfg.data_pool)]
 
     # ------------------------------------------------------------------ data
     def link(self, counter: int):
@@ -142,7 +148,13 @@ class Trainer:
                           seed=cfg.seed * 1000003 + 17, counter=counter)
 
     def frames(self, it: int, batch=None, powers_dbm=None):
-        """Symbols (device complex64 [B, nsym]), launch powers (device float32 [B]) and received waveforms."""
+        """Symbols (device complex64 [B, nsym]), launch powers (device float32 [B]) and received waveforms;
+        with a data pool, training iteration it reuses pool batch it mod data_pool."""
+        if self.pool and batch is None and powers_dbm is None:
+            return self.pool[it % len(self.pool)]
+        return self._make_frames(it, batch, powers_dbm)
+
+    def _make_frames(self, it: int, batch=None, powers_dbm=None):
         cfg = self.cfg
         B = batch or cfg.batch
         s = synth.qam16_symbols(B, cfg.nsym, cfg.seed * 7919 + it).astype(np.complex64)
@@ -223,7 +235,7 @@ class Trainer:
 
     def prune_one(self):
         """Remove the outermost tap pair of one filter (Sec. IV-C)."""
-        best = prune_choice(self.taps.cpu().numpy(), self.T, self.cfg.t_end)
+        best = prune_choice(self.taps.cpu().numpy(), self.T, self.targets)
         if best >= 0:
             self.T[best] -= 2
 

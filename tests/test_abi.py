@@ -173,3 +173,8 @@ def test_wait_probe_rejects_bad_arguments(L):
     assert L.ldbp_wait_probe(1, 0, None) == -1
     assert L.ldbp_wait_probe(1, (1 << 20) + 1, None) == -1
     assert b"limit" in L.ldbp_last_error()
+
+
+def test_ragged_set_schedule_rejects_null_plan(L):
+    assert L.ldbp_ragged_set_schedule(None, 2048, 1) == -1
+    assert b"plan" in L.ldbp_last_error()

@@ -79,6 +79,22 @@ def test_checkpoint_resume_is_bit_identical(tmp_path):
     assert np.array_equal(a.taps.cpu().numpy(), b.taps.cpu().numpy())
 
 
+def test_alternating_pruning_targets():
+    # the alternating lengths of Sec. V-B (5 at even, 3 at odd step indices):
+    # 2 + 3 + 2 + 3 pruning steps, every filter ends at its own target and the
+    # masked taps are zero
+    gpu_lib()
+    from paper_2010_14258_gb300.train import Trainer, TrainConfig
+    tr = Trainer(TrainConfig(batch=4, nsym=2048, n_spans=4, channel_steps=5, powers_dbm=(3,), t_start=9, t_end=5,
+                             t_end_odd=3, iters=40, lr=3e-4, seed=4, prune_frac=0.5))
+    assert len(tr.schedule) == 2 + 3 + 2 + 3
+    tr.fit()
+    assert tr.T == [5, 3, 5, 3]
+    h = tr.taps.cpu().numpy()
+    for i, T in enumerate(tr.T):
+        assert np.all(h[i, (T + 1) // 2:] == 0)
+
+
 def test_learnable_nonlinear_coefficients_train():
     # Remark 1: with learnable c the coefficients move and training still gains
     gpu_lib()

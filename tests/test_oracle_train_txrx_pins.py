@@ -82,6 +82,8 @@ def test_product_pruning_rule_matches_the_oracle():
         if rng.random() < 0.3:  # exact ties
             taps[:, :] = np.round(taps, 1)
         assert train.prune_choice(taps, T, target) == otrain.choose_filter(list(taps), T, [target] * M)
+        per = [int(rng.choice([1, 3, 5])) for _ in range(M)]
+        assert train.prune_choice(taps, T, per) == otrain.choose_filter(list(taps), T, per)
 
 
 @pytest.mark.parametrize("b", [0.1, 0.25, 1.0])
