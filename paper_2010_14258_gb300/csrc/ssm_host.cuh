@@ -38,6 +38,9 @@ struct DeviceProgram {
   SsmStep* steps = nullptr;
   int nsteps = 0;
   float c_pre = 0.f, noise_std = 0.f;
+  // transposed copies of tabs / tabs_lo for the L2-resident path (made on first use)
+  std::vector<float2*> st_tabs;
+  std::vector<uint32_t*> st_tabs_lo;
 };
 
 int get_program(const std::string& key, const SsmProgram& prog, std::shared_ptr<DeviceProgram>* out);
@@ -52,5 +55,9 @@ int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x
 int get_twiddle(long long n, int P, int log_n2, float2** out);
 int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, const float* wave_scale,
                 int wave_mode, uint64_t seed, uint64_t counter, cudaStream_t st);
+// L2-resident two-kernel split step (ssm_stream.cu): lengths it supports and the run.
+bool ssm_stream_supported(long long n);
+int run_program_stream(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, uint64_t seed,
+                       uint64_t counter, cudaStream_t st);
 
 }  // namespace ldbp

@@ -163,3 +163,56 @@ def test_full_size_channel_sampled(B, n, fs, spans, span_km, stps, sps):
     err, err_cufft = rel_l2(to_np(y[0:1]), ref), rel_l2(to_np(yc), ref)
     print(f"{spans * stps} steps: fused {err:.2e}, library FFT {err_cufft:.2e}")
     assert err <= 1e-4
+
+
+# ---- the L2-resident two-kernel path (n = 65536, batches of 8 or more) ----
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_l2_path_channel_matches_oracle_every_waveform(symmetric):
+    # 10 waveforms (two chunks' worth of indices in the ASE draws), 2 spans x 3 steps, ASE
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(2, 80.0, 3, symmetric, True, 5.0, 1.946e14, seed=0xABCDEF12345, counter=5)
+    x = _sig(10, 65536, 91, 2e-3)
+    y = _channel(x, fib, link, fs)
+    ref = nlse.channel(x, fib, link, fs)
+    for b in range(10):
+        assert rel_l2(y[b], ref[b]) <= 1e-5 * (2 * 3 + 1), b
+
+
+def test_l2_path_dbp_matches_oracle():
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(4, 80.0, 5, True, False)
+    x = c64(nlse.channel(_sig(8, 65536, 93, 2e-3), fib, link, fs))
+    for sym, N in ((False, 1), (True, 2)):
+        out = _dbp(x, fib, link, fs, N, sym)
+        ref = nlse.dbp(x, fib, link, fs, steps_per_span=N, symmetric=sym)
+        assert rel_l2(out, ref) <= 1e-5 * (4 * N + 1)
+
+
+def test_l2_path_long_channel_meets_tolerance():
+    # 25 x 80 km at 100 StPS with ASE (2500 steps) on the L2-resident path:
+    # waveform 0 against the oracle at the stated 1e-4
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(25, 80.0, 100, True, True, 5.0, 1.946e14, seed=77, counter=1)
+    x = _sig(8, 65536, 95, 1.585e-3)
+    y = _channel(x, fib, link, fs)
+    ref = nlse.channel(x[0:1], fib, link, fs)
+    err = rel_l2(y[0:1], ref)
+    print(f"2500 steps on the L2-resident path: {err:.2e}")
+    assert err <= 1e-4
+
+
+def test_l2_path_agrees_with_cluster_kernel():
+    # the same DBP program on 4 waveforms (cluster kernel) and on 8 (L2-resident
+    # path): two FP32 evaluations that round differently, within the stated
+    # per-step tolerance of each other (2.3e-6 measured after 25 steps)
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(25, 80.0, 1, False, False)
+    x = c64(synth.gaussian_waveform(8, 65536, 97, 1e-3))
+    a = _dbp(x[:4], fib, link, fs, 1, False)
+    b = _dbp(x, fib, link, fs, 1, False)
+    assert rel_l2(b[:4], a) <= 1e-5
