@@ -87,7 +87,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=B, help="waveforms per GPU (profiling runs use fewer)")
     ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft", "ldbp_bwd", "channel",
-                                                      "resample", "analog_channel"],
+                                                      "resample", "analog_channel", "train_channel"],
                     help="run only this kernel (warmup + steps launches) on random input, for ncu captures")
     ap.add_argument("--workload", default="ldbp",
                     choices=["ldbp", "channel", "ragged", "train", "train_prune", "sym32", "essm", "analog"],
@@ -336,6 +336,14 @@ def profile_only(args, api):
         ch = synth.Link(M_STEPS, SPAN_KM, 4, True, True)
         units = B * N_SAMP * M_STEPS * 4
         fn = lambda: api.ssm_forward(fib, ch, FS, x, out=y)  # noqa: E731
+    elif args.profile == "train_channel":
+        # the training channel's shape: --batch frames of 32768 samples, 25 x 80 km,
+        # 4 symmetric StPS with ASE (the cluster kernel with 8-block clusters)
+        xt = torch.randn(B, 32768, device="cuda", dtype=torch.complex64) * (1e-3 ** 0.5)
+        yt = torch.empty_like(xt)
+        ch = synth.Link(M_STEPS, SPAN_KM, 4, True, True)
+        units = B * 32768 * M_STEPS * 4
+        fn = lambda: api.ssm_forward(fib, ch, FS, xt, out=yt)  # noqa: E731
     elif args.profile in ("resample", "analog_channel"):
         # the analog-rate workload's grids: frames of 1024 symbols at rho_a = 6
         # (n = 6144) and rho_d = 2 (n = 2048); --batch frames, two inputs alternated
