@@ -87,7 +87,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=B, help="waveforms per GPU (profiling runs use fewer)")
     ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft", "ldbp_bwd", "channel",
-                                                      "resample", "analog_channel", "train_channel"],
+                                                      "resample", "analog_channel", "train_channel", "long_channel"],
                     help="run only this kernel (warmup + steps launches) on random input, for ncu captures")
     ap.add_argument("--workload", default="ldbp",
                     choices=["ldbp", "channel", "ragged", "train", "train_prune", "sym32", "essm", "analog"],
@@ -324,6 +324,7 @@ def profile_only(args, api):
     taps_np, c = ls_model(T)
     taps = pack_taps(taps_np)
     units = B * N_SAMP * M_STEPS
+    n_wave = N_SAMP
     if args.profile == "ldbp":
         fn = lambda: api.ldbp_apply(taps, [T] * M_STEPS, c, nxt(), out=y)  # noqa: E731
     elif args.profile == "ldbp_bwd":
@@ -343,7 +344,17 @@ def profile_only(args, api):
         yt = torch.empty_like(xt)
         ch = synth.Link(M_STEPS, SPAN_KM, 4, True, True)
         units = B * 32768 * M_STEPS * 4
+        n_wave = 32768
         fn = lambda: api.ssm_forward(fib, ch, FS, xt, out=yt)  # noqa: E731
+    elif args.profile == "long_channel":
+        # the data-generation channel's shape: --batch frames of 131072 samples,
+        # 10 x 100 km, 200 symmetric StPS with ASE (the L2-resident path from 8 frames)
+        xt = torch.randn(B, 131072, device="cuda", dtype=torch.complex64) * (1e-3 ** 0.5)
+        yt = torch.empty_like(xt)
+        ch = synth.Link(10, 100.0, 200, True, True, 5.0, 1.946e14, seed=4, counter=0)
+        units = B * 131072 * 10 * 200
+        n_wave = 131072
+        fn = lambda: api.ssm_forward(fib, ch, 128e9, xt, out=yt)  # noqa: E731
     elif args.profile in ("resample", "analog_channel"):
         # the analog-rate workload's grids: frames of 1024 symbols at rho_a = 6
         # (n = 6144) and rho_d = 2 (n = 2048); --batch frames, two inputs alternated
@@ -364,7 +375,7 @@ def profile_only(args, api):
     else:
         fn = lambda: api.ssm_cufft(fib, link, FS, x, dbp_steps_per_span=1, dbp_symmetric=False, out=y)  # noqa: E731
     ms = time_fn(fn, args.steps, args.warmup)
-    print(json.dumps({"profile": args.profile, "batch": B, "n": N_SAMP, "T": T, "ms": ms,
+    print(json.dumps({"profile": args.profile, "batch": B, "n": n_wave, "T": T, "ms": ms,
                       "samples_steps_per_s": units / (ms / 1e3)}))
 
 

@@ -1,4 +1,4 @@
-// Register-level DFT building blocks (radix 2, 3, 4, 6, 8, 12, 16) and a shared-memory
+// Register-level DFT building blocks (radix 2, 3, 4, 6, 8, 12, 16; W_32 twiddles) and a shared-memory
 // Stockham FFT for the cluster-resident split-step kernel.
 //
 // Convention: forward DFT X_k = sum_m x_m exp(-j 2 pi k m / N), natural order
@@ -209,6 +209,41 @@ __device__ __forceinline__ void dft(float2* a) {
       a[k2 + 8] = x2;
       a[k2 + 12] = x3;
     }
+  }
+}
+
+// cos(pi k / 16), k = 0..8 (head/tail splits are taken at compile time).
+constexpr double kCos16d[9] = {1.0,
+                               0.98078528040323044913,
+                               0.92387953251128675613,
+                               0.83146961230254523708,
+                               0.70710678118654752440,
+                               0.55557023301960222474,
+                               0.38268343236508977173,
+                               0.19509032201612826785,
+                               0.0};
+
+// exp(-j 2 pi k / 32) applied to v (k compile-time, 0 < k < 16); even k are
+// the 16-point constants.
+template <int k>
+__device__ __forceinline__ float2 tw32(float2 v) {
+  if constexpr ((k & 1) == 0) {
+    return tw16<k / 2>(v);
+  } else {
+    static_assert(k > 0 && k < 16, "odd k in 1..15");
+    constexpr double c = k <= 8 ? kCos16d[k] : -kCos16d[16 - k];
+    constexpr double s = k <= 8 ? kCos16d[8 - k] : kCos16d[k - 8];
+    constexpr float ch = (float)c, cl = (float)(c - (double)ch);
+    constexpr float sh = (float)s, sl = (float)(s - (double)sh);
+    return make_float2(dot_hl(v.x, ch, cl, v.y, sh, sl), dot_hl(v.y, ch, cl, -v.x, sh, sl));
+  }
+}
+
+template <int k>
+__device__ __forceinline__ void tw32_loop(float2* o) {
+  if constexpr (k < 16) {
+    o[k] = tw32<k>(o[k]);
+    tw32_loop<k + 1>(o);
   }
 }
 

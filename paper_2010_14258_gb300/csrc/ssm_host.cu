@@ -302,10 +302,10 @@ int check_link(const ldbp_fiber* f, const ldbp_link* l, double fs, const void* x
 
 int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, const float* wave_scale,
                 int wave_mode, uint64_t seed, uint64_t counter, cudaStream_t st) {
-  // Batches of n = 65536 run on the L2-resident two-kernel path: a waveform
-  // would need a 16-block cluster, and only 14 such clusters fit on the GPU
-  // at once (3/4 of the SMs).
-  if (!wave_scale && ssm_stream_supported(n) && batch >= 8)
+  // Larger batches of n = 65536 and 131072 run on the L2-resident two-kernel
+  // path: a waveform would need a 16-block cluster, and few such clusters fit
+  // on the GPU at once.
+  if (!wave_scale && ssm_stream_preferred(n, batch))
     return run_program_stream(dp, x, y, n, batch, seed, counter, st);
   int sms = 0, dev = 0;
   LDBP_CUDA_TRY(cudaGetDevice(&dev));

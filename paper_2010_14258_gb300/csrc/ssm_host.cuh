@@ -56,7 +56,7 @@ int get_twiddle(long long n, int P, int log_n2, float2** out);
 int run_program(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, const float* wave_scale,
                 int wave_mode, uint64_t seed, uint64_t counter, cudaStream_t st);
 // L2-resident two-kernel split step (ssm_stream.cu): lengths it supports and the run.
-bool ssm_stream_supported(long long n);
+bool ssm_stream_preferred(long long n, int batch);
 int run_program_stream(const DeviceProgram& dp, const void* x, void* y, long long n, int batch, uint64_t seed,
                        uint64_t counter, cudaStream_t st);
 

@@ -165,54 +165,62 @@ def test_full_size_channel_sampled(B, n, fs, spans, span_km, stps, sps):
     assert err <= 1e-4
 
 
-# ---- the L2-resident two-kernel path (n = 65536, batches of 8 or more) ----
+# ---- the L2-resident two-kernel path (n = N1 x 256 with N1 = 256, 512):
+# batches of 24 or more at n = 65536, of 8 or more at n = 131072 ----
 
+L2_CASES = [(65536, 24), (131072, 8)]
+
+
+@pytest.mark.parametrize("n,B", L2_CASES)
 @pytest.mark.parametrize("symmetric", [True, False])
-def test_l2_path_channel_matches_oracle_every_waveform(symmetric):
-    # 10 waveforms (two chunks' worth of indices in the ASE draws), 2 spans x 3 steps, ASE
+def test_l2_path_channel_matches_oracle_every_waveform(n, B, symmetric):
+    # B + 2 waveforms (distinct waveform indices in the ASE draws), 2 spans x 3 steps, ASE
     fs = 20e9
     fib = synth.Fiber()
     link = synth.Link(2, 80.0, 3, symmetric, True, 5.0, 1.946e14, seed=0xABCDEF12345, counter=5)
-    x = _sig(10, 65536, 91, 2e-3)
+    x = _sig(B + 2, n, 91, 2e-3)
     y = _channel(x, fib, link, fs)
     ref = nlse.channel(x, fib, link, fs)
-    for b in range(10):
+    for b in range(B + 2):
         assert rel_l2(y[b], ref[b]) <= 1e-5 * (2 * 3 + 1), b
 
 
-def test_l2_path_dbp_matches_oracle():
+@pytest.mark.parametrize("n,B", L2_CASES)
+def test_l2_path_dbp_matches_oracle(n, B):
     fs = 20e9
     fib = synth.Fiber()
     link = synth.Link(4, 80.0, 5, True, False)
-    x = c64(nlse.channel(_sig(8, 65536, 93, 2e-3), fib, link, fs))
+    x = c64(nlse.channel(_sig(B, n, 93, 2e-3), fib, link, fs))
     for sym, N in ((False, 1), (True, 2)):
         out = _dbp(x, fib, link, fs, N, sym)
         ref = nlse.dbp(x, fib, link, fs, steps_per_span=N, symmetric=sym)
         assert rel_l2(out, ref) <= 1e-5 * (4 * N + 1)
 
 
-def test_l2_path_long_channel_meets_tolerance():
+@pytest.mark.parametrize("n,B", L2_CASES)
+def test_l2_path_long_channel_meets_tolerance(n, B):
     # 25 x 80 km at 100 StPS with ASE (2500 steps) on the L2-resident path:
     # waveform 0 against the oracle at the stated 1e-4
     fs = 20e9
     fib = synth.Fiber()
     link = synth.Link(25, 80.0, 100, True, True, 5.0, 1.946e14, seed=77, counter=1)
-    x = _sig(8, 65536, 95, 1.585e-3)
+    x = _sig(B, n, 95, 1.585e-3)
     y = _channel(x, fib, link, fs)
     ref = nlse.channel(x[0:1], fib, link, fs)
     err = rel_l2(y[0:1], ref)
-    print(f"2500 steps on the L2-resident path: {err:.2e}")
+    print(f"2500 steps on the L2-resident path, n = {n}: {err:.2e}")
     assert err <= 1e-4
 
 
-def test_l2_path_agrees_with_cluster_kernel():
-    # the same DBP program on 4 waveforms (cluster kernel) and on 8 (L2-resident
+@pytest.mark.parametrize("n,B", L2_CASES)
+def test_l2_path_agrees_with_cluster_kernel(n, B):
+    # the same DBP program on 4 waveforms (cluster kernel) and on B (L2-resident
     # path): two FP32 evaluations that round differently, within the stated
-    # per-step tolerance of each other (2.3e-6 measured after 25 steps)
+    # per-step tolerance of each other (2.3e-6 measured after 25 steps at n = 65536)
     fs = 20e9
     fib = synth.Fiber()
     link = synth.Link(25, 80.0, 1, False, False)
-    x = c64(synth.gaussian_waveform(8, 65536, 97, 1e-3))
+    x = c64(synth.gaussian_waveform(B, n, 97, 1e-3))
     a = _dbp(x[:4], fib, link, fs, 1, False)
     b = _dbp(x, fib, link, fs, 1, False)
     assert rel_l2(b[:4], a) <= 1e-5
