@@ -185,6 +185,21 @@ def test_l2_path_channel_matches_oracle_every_waveform(n, B, symmetric):
         assert rel_l2(y[b], ref[b]) <= 1e-5 * (2 * 3 + 1), b
 
 
+@pytest.mark.parametrize("n", [65536, 131072])
+def test_l2_path_across_chunks_with_ase(n):
+    # one waveform more than a 64 MB chunk holds, twice over: the second chunk's
+    # ASE draws use the global waveform index; every waveform vs the oracle
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(2, 80.0, 3, True, True, 5.0, 1.946e14, seed=0x5EED, counter=9)
+    B = (64 << 20) // (n * 8) + 2
+    x = _sig(B, n, 99, 2e-3)
+    y = _channel(x, fib, link, fs)
+    ref = nlse.channel(x, fib, link, fs)
+    for b in range(B):
+        assert rel_l2(y[b], ref[b]) <= 1e-5 * (2 * 3 + 1), b
+
+
 @pytest.mark.parametrize("n,B", L2_CASES)
 def test_l2_path_dbp_matches_oracle(n, B):
     fs = 20e9
