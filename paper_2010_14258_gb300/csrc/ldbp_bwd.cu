@@ -299,6 +299,8 @@ static cudaError_t launch_bwd_cls(const BwdParams& p, int grid, cudaStream_t st)
 }
 
 cudaError_t launch_ldbp_bwd(const BwdParams& p, int kmax_class, cudaStream_t st) {
+  const int kf = bwd_fixed_width(p);
+  if (kf > 0) return launch_ldbp_bwd_fixed(p, kf, st);
   const int grid = p.batch * p.tiles_per_wave;
   switch (kmax_class) {
     case 2: return launch_bwd_cls<2, 1>(p, grid, st);

@@ -29,6 +29,10 @@ struct TapReduceK {
 };
 
 cudaError_t launch_ldbp_bwd(const BwdParams& p, int kmax_class, cudaStream_t st);
+// Uniform-width models (every K_i equal, 1..4) run ldbp_bwd_fix_kernel
+// (ldbp_bwd_fix.cu): K if so, else -1.
+int bwd_fixed_width(const BwdParams& p);
+cudaError_t launch_ldbp_bwd_fixed(const BwdParams& p, int K, cudaStream_t st);
 cudaError_t launch_tap_reduce(const float2* partial, int tiles, int M, int pstride, const TapReduceK& kk,
                               float2* gtaps, int taps_stride, cudaStream_t st);
 cudaError_t launch_c_reduce(const float2* partial, int tiles, int M, int pstride, float* gc, cudaStream_t st);

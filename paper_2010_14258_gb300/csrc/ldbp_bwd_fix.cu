@@ -1,0 +1,398 @@
+// Learned-DBP adjoint for models whose steps all have the same filter width
+// (T = 2K + 1 with K = 1..4): the same reverse sweep and the same per-block
+// partial sums as ldbp_bwd_kernel (Eq. (7), Sec. III-B; the Kerr and FIR
+// adjoints and the tap and c gradients are stated there), computed in a
+// layout that fits two 256-thread blocks per SM:
+//  * K is a compile-time constant (no per-step dispatch over unrolled cases);
+//  * the recomputed FIR output v of the step is staged in shared memory as
+//    [r][thread] (conflict-free), so its registers are not held across the
+//    Kerr adjoint, which is then evaluated sample by sample in place over the
+//    incoming gradient;
+//  * the tap-gradient products run in packed FP32x2 with two accumulators
+//    per tap: P += (g.re s.re, g.im s.im), Q += (g.im s.re, g.re s.im), so that
+//    sum g conj(s) = (P.x + P.y, Q.x - Q.y) with no operand swizzle per tap;
+//  * each step's checkpoint u_i is read from shared memory in an XOR-swizzled
+//    chunk order (no bank conflicts; the per-lane permutation is undone with
+//    three stages of selects).
+// The partials have the same layout as ldbp_bwd_kernel's ([blocks][M][cls + 2],
+// the c-gradient sum in the last slot), so the fixed-order reductions and the
+// allocation-free entry point are shared.
+#include "common.cuh"
+#include "ldbp_bwd.cuh"
+#include "ldbp_tile.cuh"
+
+namespace ldbp {
+
+namespace {
+
+constexpr int kR = kFwdR;            // 16 consecutive samples per thread
+constexpr int kNT = kFwdNT;          // 256 threads
+constexpr int kNW = kNT / 32;
+constexpr int kS = kR * kNT;         // 4096-sample tile
+constexpr int kNQ = kR / 2;          // float4 chunks per thread
+
+struct FixShared {
+  float2* ubuf;    // [2][kS] checkpoints (TMA destination, linear)
+  float2* vbuf;    // [kR][kNT] recomputed FIR output of the step
+  float4* taps;    // [M][K+1] (re, re, im, im)
+  float2* edges;   // [2 parity][2][kNW][kFwdEdge]
+  float2* red;     // [kNW][K+2]
+  uint64_t* bars;  // [2]
+};
+
+template <int K>
+size_t fix_smem_bytes(int M) {
+  return sizeof(float2) * ((size_t)2 * kS + (size_t)kR * kNT + 4 * kNW * kFwdEdge + (size_t)kNW * (K + 2)) +
+         sizeof(float4) * (size_t)M * (K + 1) + 32;
+}
+
+__device__ __forceinline__ bool fix_issue_load(const BwdParams& p, const FixShared& sh, int j, int i, int b,
+                                               long long g0) {
+  const long long n = p.n;
+  const float2* src = p.ckpt + ((long long)i * p.batch + b) * n;
+  float2* dst = sh.ubuf + j * kS;
+  const bool bulk = g0 >= 0 && g0 + kS <= n && aligned16(src + g0);
+  if (bulk) {
+    if (threadIdx.x == 0) {
+      mbar_arrive_expect_tx(&sh.bars[j], kS * sizeof(float2));
+      bulk_g2s(dst, src + g0, kS * sizeof(float2), &sh.bars[j]);
+    }
+  } else {
+    for (int s = threadIdx.x; s < kS; s += kNT) {
+      long long q = (g0 + s) % n;
+      if (q < 0) q += n;
+      dst[s] = src[q];
+    }
+  }
+  return bulk;
+}
+
+__device__ __forceinline__ void swap_if(bool c, float4& a, float4& b) {
+  const float4 x = a, y = b;
+  a = c ? y : x;
+  b = c ? x : y;
+}
+
+// u[r] = tile[tid * kR + r].  Lane l reads chunk q ^ (l & 7) in pass q (eight
+// consecutive lanes hit eight different 16-byte bank groups), then swaps
+// chunks across the bits of l & 7.
+__device__ __forceinline__ void load_own_samples(const float2* tile, int lane, float2 (&u)[kR]) {
+  const float4* t4 = reinterpret_cast<const float4*>(tile) + threadIdx.x * kNQ;
+  const int s = lane & 7;
+  float4 c[kNQ];
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) c[q] = t4[q ^ s];
+  // c[q] holds chunk q ^ s; undo the XOR one bit at a time
+#pragma unroll
+  for (int bit = 1; bit < kNQ; bit <<= 1) {
+    const bool sw = (s & bit) != 0;
+#pragma unroll
+    for (int q = 0; q < kNQ; ++q)
+      if ((q & bit) == 0) swap_if(sw, c[q], c[q | bit]);
+  }
+#pragma unroll
+  for (int q = 0; q < kNQ; ++q) {
+    u[2 * q] = make_float2(c[q].x, c[q].y);
+    u[2 * q + 1] = make_float2(c[q].z, c[q].w);
+  }
+}
+
+// xe = this thread's samples of the tile with K neighbours on each side
+// (zeros beyond the tile): own samples from load_own_samples, the lane
+// neighbours' by shuffles, and the outer K of lanes 0 and 31 straight from the
+// tile.  Reads shared memory only (no barrier; the tile must not change).
+template <int K>
+__device__ __forceinline__ void extend_from_tile(const float2* tile, int lane, float2 (&xe)[kR + 2 * K]) {
+  float2 u[kR];
+  load_own_samples(tile, lane, u);
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    xe[j].x = __shfl_up_sync(0xffffffffu, u[kR - K + j].x, 1);
+    xe[j].y = __shfl_up_sync(0xffffffffu, u[kR - K + j].y, 1);
+    xe[K + kR + j].x = __shfl_down_sync(0xffffffffu, u[j].x, 1);
+    xe[K + kR + j].y = __shfl_down_sync(0xffffffffu, u[j].y, 1);
+  }
+  const int base = (int)threadIdx.x * kR;
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int q = base - K + j;
+      xe[j] = q >= 0 ? tile[q] : make_float2(0.f, 0.f);
+    }
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const int q = base + kR + j;
+      xe[K + kR + j] = q < kS ? tile[q] : make_float2(0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kR; ++r) xe[K + r] = u[r];
+}
+
+// (cos, sin)(c p) for the powers of samples r, r + 1: the tier is uniform per warp.
+template <int TIER>
+__device__ __forceinline__ void rot_pair(float p0, float p1, float c, const KerrPolyA& ka, const KerrPolyB& kb,
+                                         float2& e0, float2& e1) {
+  if constexpr (TIER == 0) {
+    float2 cs, sn;
+    kerr_pair_a(make_float2(p0, p1), ka, cs, sn);
+    e0 = make_float2(cs.x, sn.x);
+    e1 = make_float2(cs.y, sn.y);
+  } else if constexpr (TIER == 1) {
+    float2 cs, sn;
+    kerr_pair_b(make_float2(p0, p1), kb, cs, sn);
+    e0 = make_float2(cs.x, sn.x);
+    e1 = make_float2(cs.y, sn.y);
+  } else {
+    e0 = expj<true>(c * p0);
+    e1 = expj<true>(c * p1);
+  }
+}
+
+// Kerr adjoint in place: g <- exp(-j c p) g - 2 c Im(w conj(g)) v with
+// p = |v|^2 and w = v exp(j c p); returns this thread's share of dl/dc (own
+// outputs only).  v is read back from the staged column vrow.
+template <int TIER>
+__device__ __forceinline__ float kerr_adjoint(float2 (&g)[kR], const float2* vrow, float c, int lo, int hi) {
+  KerrPolyA ka;
+  KerrPolyB kb;
+  if constexpr (TIER == 0) ka = kerr_poly_a(c);
+  if constexpr (TIER == 1) kb = kerr_poly_b(c);
+  float accc = 0.f;
+#pragma unroll
+  for (int r = 0; r < kR; r += 2) {
+    const float2 va[2] = {vrow[r * kNT], vrow[(r + 1) * kNT]};
+    const float pw[2] = {fmaf(va[0].x, va[0].x, va[0].y * va[0].y), fmaf(va[1].x, va[1].x, va[1].y * va[1].y)};
+    float2 e[2];
+    rot_pair<TIER>(pw[0], pw[1], c, ka, kb, e[0], e[1]);
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const float2 v = va[d];
+      const float2 w = cmul(e[d], v);
+      const float im = fmaf(w.y, g[r + d].x, -w.x * g[r + d].y);  // Im(w conj(g))
+      const float2 ge = cmulc(g[r + d], e[d]);                      // g conj(e)
+      const float k2 = -2.f * c * im;
+      g[r + d] = make_float2(fmaf(k2, v.x, ge.x), fmaf(k2, v.y, ge.y));
+      if (r + d >= lo && r + d < hi) accc = fmaf(-pw[d], im, accc);
+    }
+  }
+  return accc;
+}
+
+template <int K, int CLS>
+__global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_constant__ BwdParams p) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  FixShared sh;
+  sh.ubuf = reinterpret_cast<float2*>(smem_raw);
+  sh.vbuf = sh.ubuf + 2 * kS;
+  sh.taps = reinterpret_cast<float4*>(sh.vbuf + kR * kNT);
+  sh.edges = reinterpret_cast<float2*>(sh.taps + p.M * (K + 1));
+  sh.red = sh.edges + 4 * kNW * kFwdEdge;
+  sh.bars = reinterpret_cast<uint64_t*>(sh.red + kNW * (K + 2));
+  __shared__ int timed_out;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int b = blockIdx.x / p.tiles_per_wave;
+  const int tt = blockIdx.x - b * p.tiles_per_wave;
+  const long long n = p.n;
+  const long long t0 = (long long)tt * p.L;
+  const int Lt = (int)max(0LL, min((long long)p.L, n - t0));
+  const long long g0 = t0 - p.Hp;
+  const int s0 = tid * kR - p.Hp;
+  // samples r in [lo, hi) of this thread are outputs of this block's interval
+  const int lo = max(0, -s0), hi = min(kR, Lt - s0);
+
+  if (tid == 0) {
+    timed_out = 0;
+    mbar_init(&sh.bars[0], 1);
+    mbar_init(&sh.bars[1], 1);
+    fence_mbar_init();
+  }
+  for (int e = tid; e < p.M * (K + 1); e += kNT) {
+    const int i = e / (K + 1), k = e - i * (K + 1);
+    sh.taps[e] = tap_pair(p.taps[(long long)i * p.taps_stride + k]);
+  }
+  float2 g[kR];
+  {
+    const float2* src = p.gy + (long long)b * n;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+      long long q = (g0 + tid * kR + r) % n;
+      if (q < 0) q += n;
+      g[r] = src[q];
+    }
+  }
+  __syncthreads();
+  int phase[2] = {0, 0};
+  bool bulk[2] = {false, false};
+  bulk[(p.M - 1) & 1] = fix_issue_load(p, sh, (p.M - 1) & 1, p.M - 1, b, g0);
+  if (p.M >= 2) bulk[(p.M - 2) & 1] = fix_issue_load(p, sh, (p.M - 2) & 1, p.M - 2, b, g0);
+
+  int parity = 0;
+  float2* vrow = sh.vbuf + tid;
+  for (int i = p.M - 1; i >= 0; --i) {
+    const int j = i & 1;
+    __syncthreads();
+    if (bulk[j]) {
+      if (!mbar_wait_bounded(&sh.bars[j], phase[j])) timed_out = 1;
+      phase[j] ^= 1;
+    }
+    __syncthreads();
+    if (timed_out) break;  // uniform: read after the barrier
+    const float2* tile = sh.ubuf + j * kS;
+    const float4* h4 = sh.taps + i * (K + 1);
+    const float c = p.c[i];
+
+    // forward recompute v = A_i u (folded FIR, packed), staged in shared
+    // memory; only the largest power is kept (the Kerr tier of the warp)
+    float m = 0.f;
+    {
+      float2 xe[kR + 2 * K];
+      extend_from_tile<K>(tile, lane, xe);
+      float2 hr[K + 1], hi2[K + 1];
+#pragma unroll
+      for (int k = 0; k <= K; ++k) {
+        const float4 q = h4[k];
+        hr[k] = make_float2(q.x, q.y);
+        hi2[k] = make_float2(q.z, q.w);
+      }
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+        float2 A = __fmul2_rn(hr[0], xe[K + r]);
+        float2 Bv = __fmul2_rn(hi2[0], xe[K + r]);
+#pragma unroll
+        for (int k = 1; k <= K; ++k) {
+          const float2 sk = __fadd2_rn(xe[K + r - k], xe[K + r + k]);
+          A = __ffma2_rn(hr[k], sk, A);
+          Bv = __ffma2_rn(hi2[k], sk, Bv);
+        }
+        const float2 v = __ffma2_rn(make_float2(Bv.y, Bv.x), make_float2(-1.f, 1.f), A);
+        vrow[r * kNT] = v;
+        m = fmaxf(m, fmaf(v.x, v.x, v.y * v.y));
+      }
+    }
+    // (each thread reads back only its own column of vbuf: no barrier needed)
+    float accc = 0.f;
+    if (c != 0.f) {
+      const float mc = m * fabsf(c);
+      if (__all_sync(0xffffffffu, mc <= kKerrTierA))
+        accc = kerr_adjoint<0>(g, vrow, c, lo, hi);
+      else if (__all_sync(0xffffffffu, mc <= kKerrTierB))
+        accc = kerr_adjoint<1>(g, vrow, c, lo, hi);
+      else
+        accc = kerr_adjoint<2>(g, vrow, c, lo, hi);
+    } else {
+#pragma unroll
+      for (int r = 0; r < kR; ++r) {
+        const float2 v = vrow[r * kNT];
+        const float im = fmaf(v.y, g[r].x, -v.x * g[r].y);
+        if (r >= lo && r < hi) accc = fmaf(-fmaf(v.x, v.x, v.y * v.y), im, accc);
+      }
+    }
+
+    // tap gradients over this block's own outputs: dl/dh_k = sum g_v conj(s_k),
+    // with u_i extended again from the tile (cheaper than holding it in
+    // registers across the Kerr adjoint)
+    float2 xe[kR + 2 * K];
+    extend_from_tile<K>(tile, lane, xe);
+    float2 P[K + 1], Q[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) P[k] = Q[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+      if (r >= lo && r < hi) {
+        const float2 g1 = g[r], g2 = make_float2(g[r].y, g[r].x);
+        P[0] = __ffma2_rn(g1, xe[K + r], P[0]);
+        Q[0] = __ffma2_rn(g2, xe[K + r], Q[0]);
+#pragma unroll
+        for (int k = 1; k <= K; ++k) {
+          const float2 sk = __fadd2_rn(xe[K + r - k], xe[K + r + k]);
+          P[k] = __ffma2_rn(g1, sk, P[k]);
+          Q[k] = __ffma2_rn(g2, sk, Q[k]);
+        }
+      }
+    }
+    float2 acc[K + 1];
+#pragma unroll
+    for (int k = 0; k <= K; ++k) acc[k] = make_float2(P[k].x + P[k].y, Q[k].x - Q[k].y);
+#pragma unroll
+    for (int k = 0; k <= K; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, o);
+        acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, o);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) accc += __shfl_xor_sync(0xffffffffu, accc, o);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k <= K; ++k) sh.red[warp * (K + 2) + k] = acc[k];
+      sh.red[warp * (K + 2) + K + 1] = make_float2(accc, 0.f);
+    }
+    __syncthreads();
+    // every thread is done reading this step's tile: refill the buffer
+    if (i >= 2) bulk[j] = fix_issue_load(p, sh, j, i - 2, b, g0);
+    if (tid <= K + 1) {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int w = 0; w < kNW; ++w) s = cadd(s, sh.red[w * (K + 2) + tid]);
+      const int slot = tid <= K ? tid : CLS + 1;
+      p.partial[((long long)blockIdx.x * p.M + i) * (CLS + 2) + slot] = s;
+    }
+    // g_u = A^H g_v
+    {
+      float2 ge[kR + 2 * K];
+      float2* ef = sh.edges + parity * 2 * kNW * kFwdEdge;
+      tile_extend<K, kR, kNW>(g, ge, ef, ef + kNW * kFwdEdge, lane, warp);
+      parity ^= 1;
+      tile_fir<K, true, kR>(ge, h4, g);
+    }
+  }
+  if (timed_out) {
+    // let in-flight copies land before the block's shared memory is released
+    for (int jj = 0; jj < 2; ++jj)
+      if (bulk[jj]) mbar_wait_bounded(&sh.bars[jj], phase[jj], 1 << 16);
+    return;
+  }
+  if (p.gx) {
+    float2* dst = p.gx + (long long)b * n + t0;
+#pragma unroll
+    for (int r = 0; r < kR; ++r)
+      if (r >= lo && r < hi) dst[s0 + r] = g[r];
+  }
+}
+
+template <int K>
+cudaError_t launch_fix(const BwdParams& p, int grid, cudaStream_t st) {
+  constexpr int CLS = K <= 2 ? 2 : (K <= 4 ? 4 : (K <= 8 ? 8 : 16));
+  const size_t smem = fix_smem_bytes<K>(p.M);
+  auto kern = ldbp_bwd_fix_kernel<K, CLS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kNT, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int bwd_fixed_width(const BwdParams& p) {
+  for (int i = 1; i < p.M; ++i)
+    if (p.K[i] != p.K[0]) return -1;
+  return p.K[0] >= 1 && p.K[0] <= 4 ? p.K[0] : -1;
+}
+
+cudaError_t launch_ldbp_bwd_fixed(const BwdParams& p, int K, cudaStream_t st) {
+  const int grid = p.batch * p.tiles_per_wave;
+  switch (K) {
+    case 1: return launch_fix<1>(p, grid, st);
+    case 2: return launch_fix<2>(p, grid, st);
+    case 3: return launch_fix<3>(p, grid, st);
+    case 4: return launch_fix<4>(p, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ldbp

@@ -69,6 +69,8 @@ def _check(Ts, B, n, pw, seed, tol=1e-4):
 
 @pytest.mark.parametrize("Ts,B,n", [
     ([3] * 25, 2, 10000),
+    ([5] * 25, 2, 10000),
+    ([7] * 25, 3, 16384),
     ([5, 3] * 12 + [5], 2, 9000),
     ([9] * 25, 1, 16384),
     ([15] * 25, 1, 12000),
@@ -84,6 +86,12 @@ def test_backward_parity(Ts, B, n):
 @pytest.mark.parametrize("n", [1, 7, 64, 1023, 4097])
 def test_backward_short_and_odd(n):
     _check([5, 9, 3], 2, n, 5e-3, seed=n)
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 1023, 4097, 8193])
+def test_backward_uniform_width_short_and_odd(n):
+    # models with one width in every step run the fixed-width adjoint
+    _check([7] * 4, 2, n, 5e-3, seed=n + 1)
 
 
 def test_backward_vs_fp64_finite_differences_1024_m4():
@@ -148,7 +156,12 @@ def test_training_shape_sampled():
     _check([31] * 25, 3, 32768, 2e-3, seed=77)
 
 
-@pytest.mark.parametrize("Ts,B,n", [([9] * 25, 2, 12000), ([5, 3] * 6 + [1], 2, 9001)])
+def test_training_shape_pruned_sampled():
+    # the same shape at the end of the pruning schedule (T = 7 in every step)
+    _check([7] * 25, 3, 32768, 2e-3, seed=78)
+
+
+@pytest.mark.parametrize("Ts,B,n", [([9] * 25, 2, 12000), ([7] * 25, 2, 12001), ([5, 3] * 6 + [1], 2, 9001)])
 def test_backward_c_gradients_match_oracle(Ts, B, n):
     # Remark 1: gradients of the nonlinear coefficients (learnable scaling);
     # one linear-only layer (c = 0) still has a c-gradient
