@@ -4,10 +4,12 @@
 // adjoints and the tap and c gradients are stated there), computed in a
 // layout that fits two 256-thread blocks per SM:
 //  * K is a compile-time constant (no per-step dispatch over unrolled cases);
-//  * the recomputed FIR output v of the step is staged in shared memory as
-//    [r][thread] (conflict-free), so its registers are not held across the
-//    Kerr adjoint, which is then evaluated sample by sample in place over the
-//    incoming gradient;
+//  * one pass over sample pairs recomputes the forward FIR output v, applies
+//    the Kerr adjoint in place over the incoming gradient and accumulates the
+//    tap-gradient products, so v is never held for all samples: the rotation
+//    polynomial is chosen per pair (a warp vote) instead of from the largest
+//    power of the step; taps and polynomial coefficients are read from
+//    shared memory (broadcast);
 //  * the tap-gradient products run in packed FP32x2 with two accumulators
 //    per tap: P += (g.re s.re, g.im s.im), Q += (g.im s.re, g.re s.im), so that
 //    sum g conj(s) = (P.x + P.y, Q.x - Q.y) with no operand swizzle per tap;
@@ -33,7 +35,7 @@ constexpr int kNQ = kR / 2;          // float4 chunks per thread
 
 struct FixShared {
   float2* ubuf;    // [2][kS] checkpoints (TMA destination, linear)
-  float2* vbuf;    // [kR][kNT] recomputed FIR output of the step
+  float* kerr;     // [M][8] degree-8/7 rotation polynomial of every step (KerrPolyB)
   float4* taps;    // [M][K+1] (re, re, im, im)
   float2* edges;   // [2 parity][2][kNW][kFwdEdge]
   float2* red;     // [kNW][K+2]
@@ -42,8 +44,8 @@ struct FixShared {
 
 template <int K>
 size_t fix_smem_bytes(int M) {
-  return sizeof(float2) * ((size_t)2 * kS + (size_t)kR * kNT + 4 * kNW * kFwdEdge + (size_t)kNW * (K + 2)) +
-         sizeof(float4) * (size_t)M * (K + 1) + 32;
+  return sizeof(float2) * ((size_t)2 * kS + 4 * kNW * kFwdEdge + (size_t)kNW * (K + 2)) +
+         sizeof(float4) * (size_t)M * (K + 1) + sizeof(float) * 8 * (size_t)M + 32;
 }
 
 __device__ __forceinline__ bool fix_issue_load(const BwdParams& p, const FixShared& sh, int j, int i, int b,
@@ -131,66 +133,16 @@ __device__ __forceinline__ void extend_from_tile(const float2* tile, int lane, f
   for (int r = 0; r < kR; ++r) xe[K + r] = u[r];
 }
 
-// (cos, sin)(c p) for the powers of samples r, r + 1: the tier is uniform per warp.
-template <int TIER>
-__device__ __forceinline__ void rot_pair(float p0, float p1, float c, const KerrPolyA& ka, const KerrPolyB& kb,
-                                         float2& e0, float2& e1) {
-  if constexpr (TIER == 0) {
-    float2 cs, sn;
-    kerr_pair_a(make_float2(p0, p1), ka, cs, sn);
-    e0 = make_float2(cs.x, sn.x);
-    e1 = make_float2(cs.y, sn.y);
-  } else if constexpr (TIER == 1) {
-    float2 cs, sn;
-    kerr_pair_b(make_float2(p0, p1), kb, cs, sn);
-    e0 = make_float2(cs.x, sn.x);
-    e1 = make_float2(cs.y, sn.y);
-  } else {
-    e0 = expj<true>(c * p0);
-    e1 = expj<true>(c * p1);
-  }
-}
-
-// Kerr adjoint in place: g <- exp(-j c p) g - 2 c Im(w conj(g)) v with
-// p = |v|^2 and w = v exp(j c p); returns this thread's share of dl/dc (own
-// outputs only).  v is read back from the staged column vrow.
-template <int TIER>
-__device__ __forceinline__ float kerr_adjoint(float2 (&g)[kR], const float2* vrow, float c, int lo, int hi) {
-  KerrPolyA ka;
-  KerrPolyB kb;
-  if constexpr (TIER == 0) ka = kerr_poly_a(c);
-  if constexpr (TIER == 1) kb = kerr_poly_b(c);
-  float accc = 0.f;
-#pragma unroll
-  for (int r = 0; r < kR; r += 2) {
-    const float2 va[2] = {vrow[r * kNT], vrow[(r + 1) * kNT]};
-    const float pw[2] = {fmaf(va[0].x, va[0].x, va[0].y * va[0].y), fmaf(va[1].x, va[1].x, va[1].y * va[1].y)};
-    float2 e[2];
-    rot_pair<TIER>(pw[0], pw[1], c, ka, kb, e[0], e[1]);
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      const float2 v = va[d];
-      const float2 w = cmul(e[d], v);
-      const float im = fmaf(w.y, g[r + d].x, -w.x * g[r + d].y);  // Im(w conj(g))
-      const float2 ge = cmulc(g[r + d], e[d]);                      // g conj(e)
-      const float k2 = -2.f * c * im;
-      g[r + d] = make_float2(fmaf(k2, v.x, ge.x), fmaf(k2, v.y, ge.y));
-      if (r + d >= lo && r + d < hi) accc = fmaf(-pw[d], im, accc);
-    }
-  }
-  return accc;
-}
-
 template <int K, int CLS>
 __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_constant__ BwdParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FixShared sh;
   sh.ubuf = reinterpret_cast<float2*>(smem_raw);
-  sh.vbuf = sh.ubuf + 2 * kS;
-  sh.taps = reinterpret_cast<float4*>(sh.vbuf + kR * kNT);
+  sh.taps = reinterpret_cast<float4*>(sh.ubuf + 2 * kS);
   sh.edges = reinterpret_cast<float2*>(sh.taps + p.M * (K + 1));
   sh.red = sh.edges + 4 * kNW * kFwdEdge;
   sh.bars = reinterpret_cast<uint64_t*>(sh.red + kNW * (K + 2));
+  sh.kerr = reinterpret_cast<float*>(sh.bars + 2);
   __shared__ int timed_out;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -214,6 +166,7 @@ __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_const
     const int i = e / (K + 1), k = e - i * (K + 1);
     sh.taps[e] = tap_pair(p.taps[(long long)i * p.taps_stride + k]);
   }
+  for (int i = tid; i < p.M; i += kNT) *reinterpret_cast<KerrPolyB*>(sh.kerr + i * 8) = kerr_poly_b(p.c[i]);
   float2 g[kR];
   {
     const float2* src = p.gy + (long long)b * n;
@@ -231,7 +184,6 @@ __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_const
   if (p.M >= 2) bulk[(p.M - 2) & 1] = fix_issue_load(p, sh, (p.M - 2) & 1, p.M - 2, b, g0);
 
   int parity = 0;
-  float2* vrow = sh.vbuf + tid;
   for (int i = p.M - 1; i >= 0; --i) {
     const int j = i & 1;
     __syncthreads();
@@ -245,72 +197,76 @@ __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_const
     const float4* h4 = sh.taps + i * (K + 1);
     const float c = p.c[i];
 
-    // forward recompute v = A_i u (folded FIR, packed), staged in shared
-    // memory; only the largest power is kept (the Kerr tier of the warp)
-    float m = 0.f;
-    {
-      float2 xe[kR + 2 * K];
-      extend_from_tile<K>(tile, lane, xe);
-      float2 hr[K + 1], hi2[K + 1];
-#pragma unroll
-      for (int k = 0; k <= K; ++k) {
-        const float4 q = h4[k];
-        hr[k] = make_float2(q.x, q.y);
-        hi2[k] = make_float2(q.z, q.w);
-      }
-#pragma unroll
-      for (int r = 0; r < kR; ++r) {
-        float2 A = __fmul2_rn(hr[0], xe[K + r]);
-        float2 Bv = __fmul2_rn(hi2[0], xe[K + r]);
-#pragma unroll
-        for (int k = 1; k <= K; ++k) {
-          const float2 sk = __fadd2_rn(xe[K + r - k], xe[K + r + k]);
-          A = __ffma2_rn(hr[k], sk, A);
-          Bv = __ffma2_rn(hi2[k], sk, Bv);
-        }
-        const float2 v = __ffma2_rn(make_float2(Bv.y, Bv.x), make_float2(-1.f, 1.f), A);
-        vrow[r * kNT] = v;
-        m = fmaxf(m, fmaf(v.x, v.x, v.y * v.y));
-      }
-    }
-    // (each thread reads back only its own column of vbuf: no barrier needed)
-    float accc = 0.f;
-    if (c != 0.f) {
-      const float mc = m * fabsf(c);
-      if (__all_sync(0xffffffffu, mc <= kKerrTierA))
-        accc = kerr_adjoint<0>(g, vrow, c, lo, hi);
-      else if (__all_sync(0xffffffffu, mc <= kKerrTierB))
-        accc = kerr_adjoint<1>(g, vrow, c, lo, hi);
-      else
-        accc = kerr_adjoint<2>(g, vrow, c, lo, hi);
-    } else {
-#pragma unroll
-      for (int r = 0; r < kR; ++r) {
-        const float2 v = vrow[r * kNT];
-        const float im = fmaf(v.y, g[r].x, -v.x * g[r].y);
-        if (r >= lo && r < hi) accc = fmaf(-fmaf(v.x, v.x, v.y * v.y), im, accc);
-      }
-    }
-
-    // tap gradients over this block's own outputs: dl/dh_k = sum g_v conj(s_k),
-    // with u_i extended again from the tile (cheaper than holding it in
-    // registers across the Kerr adjoint)
+    // One pass over sample pairs: the recomputed forward output v = A_i u
+    // (folded FIR, packed), the Kerr adjoint in place over the gradient, and
+    // the tap-gradient products dl/dh_k += g_v conj(s_k).  The rotation uses
+    // the degree-8/7 polynomials (|c p| <= 1) when every lane's pair is in
+    // range, else the range-reducing path, decided per pair and per warp.
     float2 xe[kR + 2 * K];
     extend_from_tile<K>(tile, lane, xe);
     float2 P[K + 1], Q[K + 1];
 #pragma unroll
     for (int k = 0; k <= K; ++k) P[k] = Q[k] = make_float2(0.f, 0.f);
+    float accc = 0.f;
+    const float cabs = fabsf(c);
 #pragma unroll
-    for (int r = 0; r < kR; ++r) {
-      if (r >= lo && r < hi) {
-        const float2 g1 = g[r], g2 = make_float2(g[r].y, g[r].x);
-        P[0] = __ffma2_rn(g1, xe[K + r], P[0]);
-        Q[0] = __ffma2_rn(g2, xe[K + r], Q[0]);
+    for (int r = 0; r < kR; r += 2) {
+      float2 v[2];
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const float4 q0 = h4[0];
+        float2 A = __fmul2_rn(make_float2(q0.x, q0.y), xe[K + r + d]);
+        float2 Bv = __fmul2_rn(make_float2(q0.z, q0.w), xe[K + r + d]);
 #pragma unroll
         for (int k = 1; k <= K; ++k) {
-          const float2 sk = __fadd2_rn(xe[K + r - k], xe[K + r + k]);
-          P[k] = __ffma2_rn(g1, sk, P[k]);
-          Q[k] = __ffma2_rn(g2, sk, Q[k]);
+          const float4 q = h4[k];
+          const float2 sk = __fadd2_rn(xe[K + r + d - k], xe[K + r + d + k]);
+          A = __ffma2_rn(make_float2(q.x, q.y), sk, A);
+          Bv = __ffma2_rn(make_float2(q.z, q.w), sk, Bv);
+        }
+        v[d] = __ffma2_rn(make_float2(Bv.y, Bv.x), make_float2(-1.f, 1.f), A);
+      }
+      const float pw0 = fmaf(v[0].x, v[0].x, v[0].y * v[0].y), pw1 = fmaf(v[1].x, v[1].x, v[1].y * v[1].y);
+      if (c != 0.f) {
+        float2 e[2];
+        if (__all_sync(0xffffffffu, cabs * fmaxf(pw0, pw1) <= kKerrTierB)) {
+          const KerrPolyB kb = *reinterpret_cast<const KerrPolyB*>(sh.kerr + i * 8);
+          float2 cs, sn;
+          kerr_pair_b(make_float2(pw0, pw1), kb, cs, sn);
+          e[0] = make_float2(cs.x, sn.x);
+          e[1] = make_float2(cs.y, sn.y);
+        } else {
+          e[0] = expj<true>(c * pw0);
+          e[1] = expj<true>(c * pw1);
+        }
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          const float2 w = cmul(e[d], v[d]);
+          const float im = fmaf(w.y, g[r + d].x, -w.x * g[r + d].y);  // Im(w conj(g))
+          const float2 ge = cmulc(g[r + d], e[d]);                      // g conj(e)
+          const float k2 = -2.f * c * im;
+          g[r + d] = make_float2(fmaf(k2, v[d].x, ge.x), fmaf(k2, v[d].y, ge.y));
+          if (r + d >= lo && r + d < hi) accc = fmaf(-(d ? pw1 : pw0), im, accc);
+        }
+      } else {
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          const float im = fmaf(v[d].y, g[r + d].x, -v[d].x * g[r + d].y);
+          if (r + d >= lo && r + d < hi) accc = fmaf(-(d ? pw1 : pw0), im, accc);
+        }
+      }
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        if (r + d >= lo && r + d < hi) {
+          const float2 g1 = g[r + d], g2 = make_float2(g1.y, g1.x);
+          P[0] = __ffma2_rn(g1, xe[K + r + d], P[0]);
+          Q[0] = __ffma2_rn(g2, xe[K + r + d], Q[0]);
+#pragma unroll
+          for (int k = 1; k <= K; ++k) {
+            const float2 sk = __fadd2_rn(xe[K + r + d - k], xe[K + r + d + k]);
+            P[k] = __ffma2_rn(g1, sk, P[k]);
+            Q[k] = __ffma2_rn(g2, sk, Q[k]);
+          }
         }
       }
     }
