@@ -205,15 +205,7 @@ __global__ void __launch_bounds__(kFwdNT, MINB) ldbp_bwd_kernel(const __grid_con
       phase[j] ^= 1;
     }
     float2 u[kFwdR];
-    {
-      const float4* t4 = reinterpret_cast<const float4*>(sh.ubuf + j * kFwdS + tid * kFwdR);
-#pragma unroll
-      for (int r = 0; r < kFwdR / 2; ++r) {
-        const float4 q = t4[r];
-        u[2 * r] = make_float2(q.x, q.y);
-        u[2 * r + 1] = make_float2(q.z, q.w);
-      }
-    }
+    load_own_samples<kFwdR>(sh.ubuf + j * kFwdS, lane, u);
     __syncthreads();
     if (timed_out) break;  // uniform: read after the barrier
     if (i >= 2) bulk[j] = issue_ckpt_load(p, sh, j, i - 2, b, g0);

@@ -69,36 +69,6 @@ __device__ __forceinline__ bool fix_issue_load(const BwdParams& p, const FixShar
   return bulk;
 }
 
-__device__ __forceinline__ void swap_if(bool c, float4& a, float4& b) {
-  const float4 x = a, y = b;
-  a = c ? y : x;
-  b = c ? x : y;
-}
-
-// u[r] = tile[tid * kR + r].  Lane l reads chunk q ^ (l & 7) in pass q (eight
-// consecutive lanes hit eight different 16-byte bank groups), then swaps
-// chunks across the bits of l & 7.
-__device__ __forceinline__ void load_own_samples(const float2* tile, int lane, float2 (&u)[kR]) {
-  const float4* t4 = reinterpret_cast<const float4*>(tile) + threadIdx.x * kNQ;
-  const int s = lane & 7;
-  float4 c[kNQ];
-#pragma unroll
-  for (int q = 0; q < kNQ; ++q) c[q] = t4[q ^ s];
-  // c[q] holds chunk q ^ s; undo the XOR one bit at a time
-#pragma unroll
-  for (int bit = 1; bit < kNQ; bit <<= 1) {
-    const bool sw = (s & bit) != 0;
-#pragma unroll
-    for (int q = 0; q < kNQ; ++q)
-      if ((q & bit) == 0) swap_if(sw, c[q], c[q | bit]);
-  }
-#pragma unroll
-  for (int q = 0; q < kNQ; ++q) {
-    u[2 * q] = make_float2(c[q].x, c[q].y);
-    u[2 * q + 1] = make_float2(c[q].z, c[q].w);
-  }
-}
-
 // xe = this thread's samples of the tile with K neighbours on each side
 // (zeros beyond the tile): own samples from load_own_samples, the lane
 // neighbours' by shuffles, and the outer K of lanes 0 and 31 straight from the

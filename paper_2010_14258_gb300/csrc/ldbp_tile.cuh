@@ -47,6 +47,41 @@ __device__ __forceinline__ void tile_extend(const float2 (&v)[R], float2 (&xe)[R
   for (int r = 0; r < R; ++r) xe[K + r] = v[r];
 }
 
+__device__ __forceinline__ void swap_if(bool c, float4& a, float4& b) {
+  const float4 x = a, y = b;
+  a = c ? y : x;
+  b = c ? x : y;
+}
+
+// u[r] = tile[threadIdx.x * R + r] from shared memory without bank
+// conflicts: lane l reads 16-byte chunk q ^ (l & 7) in pass q (eight
+// consecutive lanes hit eight different bank groups instead of one), then
+// the chunks are swapped back across the bits of l & 7 (three stages of
+// selects).  R is a multiple of 16.
+template <int R>
+__device__ __forceinline__ void load_own_samples(const float2* tile, int lane, float2 (&u)[R]) {
+  static_assert(R % 16 == 0, "eight or more 16-byte chunks per thread");
+  constexpr int NQ = R / 2;
+  const float4* t4 = reinterpret_cast<const float4*>(tile) + threadIdx.x * NQ;
+  const int s = lane & 7;
+  float4 c[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) c[q] = t4[q ^ s];
+  // c[q] holds chunk q ^ s; undo the XOR one bit at a time
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1) {
+    const bool sw = (s & bit) != 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if ((q & bit) == 0) swap_if(sw, c[q], c[q | bit]);
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    u[2 * q] = make_float2(c[q].x, c[q].y);
+    u[2 * q + 1] = make_float2(c[q].z, c[q].w);
+  }
+}
+
 // Taps pre-expanded for packed FP32x2 arithmetic: (h.re, h.re, h.im, h.im).
 __device__ __forceinline__ float4 tap_pair(float2 h) { return make_float4(h.x, h.x, h.y, h.y); }
 
