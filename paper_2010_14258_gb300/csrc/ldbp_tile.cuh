@@ -82,6 +82,29 @@ __device__ __forceinline__ void load_own_samples(const float2* tile, int lane, f
   }
 }
 
+// tile[threadIdx.x * R + r] = v[r], the inverse of load_own_samples: the
+// chunks are permuted first, then pass q writes chunk q ^ (l & 7).
+template <int R>
+__device__ __forceinline__ void store_own_samples(float2* tile, int lane, const float2 (&v)[R]) {
+  static_assert(R % 16 == 0, "eight or more 16-byte chunks per thread");
+  constexpr int NQ = R / 2;
+  float4* t4 = reinterpret_cast<float4*>(tile) + threadIdx.x * NQ;
+  const int s = lane & 7;
+  float4 c[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) c[q] = make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+#pragma unroll
+  for (int bit = 1; bit < 8; bit <<= 1) {
+    const bool sw = (s & bit) != 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      if ((q & bit) == 0) swap_if(sw, c[q], c[q | bit]);
+  }
+  // c[q] now holds chunk q ^ s
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) t4[q ^ s] = c[q];
+}
+
 // Taps pre-expanded for packed FP32x2 arithmetic: (h.re, h.re, h.im, h.im).
 __device__ __forceinline__ float4 tap_pair(float2 h) { return make_float4(h.x, h.x, h.y, h.y); }
 
