@@ -307,7 +307,11 @@ __global__ void __launch_bounds__(kENT, 1) ldbp_essm_bwd_kernel(const __grid_con
       phase[j] ^= 1;
     }
     float2 u[kER];
-    {
+    if constexpr (KAPPA <= 8) {
+      load_own_samples<kER>(sh.ubuf + j * kES, lane, u);  // conflict-free swizzled read
+    } else {
+      // the wide-filter classes keep the plain read (the swizzle's registers
+      // made them spill more: kappa = 20 8 % slower)
       const float4* t4 = reinterpret_cast<const float4*>(sh.ubuf + j * kES + tid * kER);
 #pragma unroll
       for (int r = 0; r < kER / 2; ++r) {

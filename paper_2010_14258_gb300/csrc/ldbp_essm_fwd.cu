@@ -150,15 +150,7 @@ __global__ void __launch_bounds__(kENT, 2) ldbp_essm_kernel(const __grid_constan
   if (timed_out) return;
 
   float2 v[kER];
-  {
-    const float4* t4 = reinterpret_cast<const float4*>(tile + tid * kER);
-#pragma unroll
-    for (int r = 0; r < kER / 2; ++r) {
-      const float4 q = t4[r];
-      v[2 * r] = make_float2(q.x, q.y);
-      v[2 * r + 1] = make_float2(q.z, q.w);
-    }
-  }
+  load_own_samples<kER>(tile, lane, v);  // conflict-free swizzled read
   int parity = 0;
   const int s0 = tid * kER - p.Hp;  // output offset of v[0]
   for (int i = 0; i < p.M; ++i) {
@@ -175,11 +167,7 @@ __global__ void __launch_bounds__(kENT, 2) ldbp_essm_kernel(const __grid_constan
     if (p.K[i] > 0) parity ^= 1;
   }
 
-  {
-    float4* t4 = reinterpret_cast<float4*>(tile + tid * kER);
-#pragma unroll
-    for (int r = 0; r < kER / 2; ++r) t4[r] = make_float4(v[2 * r].x, v[2 * r].y, v[2 * r + 1].x, v[2 * r + 1].y);
-  }
+  store_own_samples<kER>(tile, lane, v);
   float2* dst = p.y + (long long)b * n + t0;
   if (aligned16(dst) && aligned16(tile + p.Hp) && (Lt % 2 == 0)) {
     fence_proxy_async_smem();
