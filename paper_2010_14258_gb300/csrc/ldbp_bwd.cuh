@@ -29,10 +29,12 @@ struct TapReduceK {
 };
 
 cudaError_t launch_ldbp_bwd(const BwdParams& p, int kmax_class, cudaStream_t st);
-// Uniform-width models (every K_i equal, 1..4) run ldbp_bwd_fix_kernel
-// (ldbp_bwd_fix.cu): K if so, else -1.
+// Models with every K_i <= 4 run ldbp_bwd_fix_kernel (ldbp_bwd_fix.cu):
+// bwd_fixed_width returns the instance to launch (K for one width 1..4 in
+// every step, kFixMixed + class for mixed widths of class 2 or 4), else -1.
+constexpr int kFixMixed = 100;
 int bwd_fixed_width(const BwdParams& p);
-cudaError_t launch_ldbp_bwd_fixed(const BwdParams& p, int K, cudaStream_t st);
+cudaError_t launch_ldbp_bwd_fixed(const BwdParams& p, int sel, cudaStream_t st);
 cudaError_t launch_tap_reduce(const float2* partial, int tiles, int M, int pstride, const TapReduceK& kk,
                               float2* gtaps, int taps_stride, cudaStream_t st);
 cudaError_t launch_c_reduce(const float2* partial, int tiles, int M, int pstride, float* gc, cudaStream_t st);

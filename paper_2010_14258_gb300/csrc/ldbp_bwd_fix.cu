@@ -1,9 +1,10 @@
-// Learned-DBP adjoint for models whose steps all have the same filter width
-// (T = 2K + 1 with K = 1..4): the same reverse sweep and the same per-block
+// Learned-DBP adjoint for models whose filters have half-widths K_i <= 4
+// (T_i <= 9; one width in every step, or mixed): the same reverse sweep and the same per-block
 // partial sums as ldbp_bwd_kernel (Eq. (7), Sec. III-B; the Kerr and FIR
 // adjoints and the tap and c gradients are stated there), computed in a
 // layout that fits two 256-thread blocks per SM:
-//  * K is a compile-time constant (no per-step dispatch over unrolled cases);
+//  * K is a compile-time constant of the step (one instance for a uniform
+//    model; a per-step switch over K = 0..4 otherwise);
 //  * one pass over sample pairs recomputes the forward FIR output v, applies
 //    the Kerr adjoint in place over the incoming gradient and accumulates the
 //    tap-gradient products, so v is never held for all samples: the rotation
@@ -36,9 +37,9 @@ constexpr int kNQ = kR / 2;          // float4 chunks per thread
 struct FixShared {
   float2* ubuf;    // [2][kS] checkpoints (TMA destination, linear)
   float* kerr;     // [M][8] degree-8/7 rotation polynomial of every step (KerrPolyB)
-  float4* taps;    // [M][K+1] (re, re, im, im)
+  float4* taps;    // [M][KC+1] (re, re, im, im), zero beyond K_i
   float2* edges;   // [2 parity][2][kNW][kFwdEdge]
-  float2* red;     // [kNW][K+2]
+  float2* red;     // [kNW][KC+2]
   uint64_t* bars;  // [2]
 };
 
@@ -103,15 +104,138 @@ __device__ __forceinline__ void extend_from_tile(const float2* tile, int lane, f
   for (int r = 0; r < kR; ++r) xe[K + r] = u[r];
 }
 
-template <int K, int CLS>
+// One step i of the reverse sweep for a filter of half-width K (taps row h4
+// zero-padded to the class width KC): the fused pass over sample pairs, the
+// block's tap and c sums (written to the partials), and the conjugate FIR
+// g <- A_i^H g_v.  Reads the step's checkpoint tile and, once every thread is
+// past the reduction barrier, refills its buffer with step i - 2.
+template <int K, int KC>
+__device__ __forceinline__ void fix_step(const BwdParams& p, int i, const float2* tile, const float4* h4,
+                                         const KerrPolyB* kpoly, float2 (&g)[kR], const FixShared& sh, int& parity,
+                                         int lo, int hi, int lane, int warp, int tid, int b, long long g0,
+                                         bool& bulk_j) {
+  float2* const red = sh.red;
+  const float c = p.c[i];
+  // One pass over sample pairs: the recomputed forward output v = A_i u
+  // (folded FIR, packed), the Kerr adjoint in place over the gradient, and
+  // the tap-gradient products dl/dh_k += g_v conj(s_k).  The rotation uses
+  // the degree-8/7 polynomials (|c p| <= 1) when every lane's pair is in
+  // range, else the range-reducing path, decided per pair and per warp.
+  float2 xe[kR + 2 * K];
+  extend_from_tile<K>(tile, lane, xe);
+  float2 P[K + 1], Q[K + 1];
+#pragma unroll
+  for (int k = 0; k <= K; ++k) P[k] = Q[k] = make_float2(0.f, 0.f);
+  float accc = 0.f;
+  const float cabs = fabsf(c);
+#pragma unroll
+  for (int r = 0; r < kR; r += 2) {
+    float2 v[2];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const float4 q0 = h4[0];
+      float2 A = __fmul2_rn(make_float2(q0.x, q0.y), xe[K + r + d]);
+      float2 Bv = __fmul2_rn(make_float2(q0.z, q0.w), xe[K + r + d]);
+#pragma unroll
+      for (int k = 1; k <= K; ++k) {
+        const float4 q = h4[k];
+        const float2 sk = __fadd2_rn(xe[K + r + d - k], xe[K + r + d + k]);
+        A = __ffma2_rn(make_float2(q.x, q.y), sk, A);
+        Bv = __ffma2_rn(make_float2(q.z, q.w), sk, Bv);
+      }
+      v[d] = __ffma2_rn(make_float2(Bv.y, Bv.x), make_float2(-1.f, 1.f), A);
+    }
+    const float pw0 = fmaf(v[0].x, v[0].x, v[0].y * v[0].y), pw1 = fmaf(v[1].x, v[1].x, v[1].y * v[1].y);
+    if (c != 0.f) {
+      float2 e[2];
+      if (__all_sync(0xffffffffu, cabs * fmaxf(pw0, pw1) <= kKerrTierB)) {
+        const KerrPolyB kb = *kpoly;
+        float2 cs, sn;
+        kerr_pair_b(make_float2(pw0, pw1), kb, cs, sn);
+        e[0] = make_float2(cs.x, sn.x);
+        e[1] = make_float2(cs.y, sn.y);
+      } else {
+        e[0] = expj<true>(c * pw0);
+        e[1] = expj<true>(c * pw1);
+      }
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const float2 w = cmul(e[d], v[d]);
+        const float im = fmaf(w.y, g[r + d].x, -w.x * g[r + d].y);  // Im(w conj(g))
+        const float2 ge = cmulc(g[r + d], e[d]);                      // g conj(e)
+        const float k2 = -2.f * c * im;
+        g[r + d] = make_float2(fmaf(k2, v[d].x, ge.x), fmaf(k2, v[d].y, ge.y));
+        if (r + d >= lo && r + d < hi) accc = fmaf(-(d ? pw1 : pw0), im, accc);
+      }
+    } else {
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const float im = fmaf(v[d].y, g[r + d].x, -v[d].x * g[r + d].y);
+        if (r + d >= lo && r + d < hi) accc = fmaf(-(d ? pw1 : pw0), im, accc);
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      if (r + d >= lo && r + d < hi) {
+        const float2 g1 = g[r + d], g2 = make_float2(g1.y, g1.x);
+        P[0] = __ffma2_rn(g1, xe[K + r + d], P[0]);
+        Q[0] = __ffma2_rn(g2, xe[K + r + d], Q[0]);
+#pragma unroll
+        for (int k = 1; k <= K; ++k) {
+          const float2 sk = __fadd2_rn(xe[K + r + d - k], xe[K + r + d + k]);
+          P[k] = __ffma2_rn(g1, sk, P[k]);
+          Q[k] = __ffma2_rn(g2, sk, Q[k]);
+        }
+      }
+    }
+  }
+  float2 acc[K + 1];
+#pragma unroll
+  for (int k = 0; k <= K; ++k) acc[k] = make_float2(P[k].x + P[k].y, Q[k].x - Q[k].y);
+#pragma unroll
+  for (int k = 0; k <= K; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, o);
+      acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, o);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) accc += __shfl_xor_sync(0xffffffffu, accc, o);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k <= K; ++k) red[warp * (KC + 2) + k] = acc[k];
+    red[warp * (KC + 2) + KC + 1] = make_float2(accc, 0.f);
+  }
+  __syncthreads();
+  // every thread is done reading this step's tile: refill the buffer
+  const int j = i & 1;
+  if (i >= 2) bulk_j = fix_issue_load(p, sh, j, i - 2, b, g0);
+  if (tid <= K || tid == KC + 1) {
+    float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) s = cadd(s, red[w * (KC + 2) + tid]);
+    p.partial[((long long)blockIdx.x * p.M + i) * (KC + 2) + tid] = s;
+  }
+  // g_u = A^H g_v
+  float2 ge[kR + 2 * K];
+  float2* ef = sh.edges + parity * 2 * kNW * kFwdEdge;
+  tile_extend<K, kR, kNW>(g, ge, ef, ef + kNW * kFwdEdge, lane, warp);
+  if (K > 0) parity ^= 1;
+  tile_fir<K, true, kR>(ge, h4, g);
+}
+
+// KFIX >= 0: every step has half-width KFIX (= KC); KFIX < 0: per-step
+// dispatch over the half-widths 0..KC (uniform per block).
+template <int KC, int KFIX>
 __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_constant__ BwdParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FixShared sh;
   sh.ubuf = reinterpret_cast<float2*>(smem_raw);
   sh.taps = reinterpret_cast<float4*>(sh.ubuf + 2 * kS);
-  sh.edges = reinterpret_cast<float2*>(sh.taps + p.M * (K + 1));
+  sh.edges = reinterpret_cast<float2*>(sh.taps + p.M * (KC + 1));
   sh.red = sh.edges + 4 * kNW * kFwdEdge;
-  sh.bars = reinterpret_cast<uint64_t*>(sh.red + kNW * (K + 2));
+  sh.bars = reinterpret_cast<uint64_t*>(sh.red + kNW * (KC + 2));
   sh.kerr = reinterpret_cast<float*>(sh.bars + 2);
   __shared__ int timed_out;
 
@@ -132,9 +256,9 @@ __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_const
     mbar_init(&sh.bars[1], 1);
     fence_mbar_init();
   }
-  for (int e = tid; e < p.M * (K + 1); e += kNT) {
-    const int i = e / (K + 1), k = e - i * (K + 1);
-    sh.taps[e] = tap_pair(p.taps[(long long)i * p.taps_stride + k]);
+  for (int e = tid; e < p.M * (KC + 1); e += kNT) {
+    const int i = e / (KC + 1), k = e - i * (KC + 1);
+    sh.taps[e] = tap_pair(k <= p.K[i] ? p.taps[(long long)i * p.taps_stride + k] : make_float2(0.f, 0.f));
   }
   for (int i = tid; i < p.M; i += kNT) *reinterpret_cast<KerrPolyB*>(sh.kerr + i * 8) = kerr_poly_b(p.c[i]);
   float2 g[kR];
@@ -164,118 +288,27 @@ __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_const
     __syncthreads();
     if (timed_out) break;  // uniform: read after the barrier
     const float2* tile = sh.ubuf + j * kS;
-    const float4* h4 = sh.taps + i * (K + 1);
-    const float c = p.c[i];
-
-    // One pass over sample pairs: the recomputed forward output v = A_i u
-    // (folded FIR, packed), the Kerr adjoint in place over the gradient, and
-    // the tap-gradient products dl/dh_k += g_v conj(s_k).  The rotation uses
-    // the degree-8/7 polynomials (|c p| <= 1) when every lane's pair is in
-    // range, else the range-reducing path, decided per pair and per warp.
-    float2 xe[kR + 2 * K];
-    extend_from_tile<K>(tile, lane, xe);
-    float2 P[K + 1], Q[K + 1];
-#pragma unroll
-    for (int k = 0; k <= K; ++k) P[k] = Q[k] = make_float2(0.f, 0.f);
-    float accc = 0.f;
-    const float cabs = fabsf(c);
-#pragma unroll
-    for (int r = 0; r < kR; r += 2) {
-      float2 v[2];
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        const float4 q0 = h4[0];
-        float2 A = __fmul2_rn(make_float2(q0.x, q0.y), xe[K + r + d]);
-        float2 Bv = __fmul2_rn(make_float2(q0.z, q0.w), xe[K + r + d]);
-#pragma unroll
-        for (int k = 1; k <= K; ++k) {
-          const float4 q = h4[k];
-          const float2 sk = __fadd2_rn(xe[K + r + d - k], xe[K + r + d + k]);
-          A = __ffma2_rn(make_float2(q.x, q.y), sk, A);
-          Bv = __ffma2_rn(make_float2(q.z, q.w), sk, Bv);
-        }
-        v[d] = __ffma2_rn(make_float2(Bv.y, Bv.x), make_float2(-1.f, 1.f), A);
-      }
-      const float pw0 = fmaf(v[0].x, v[0].x, v[0].y * v[0].y), pw1 = fmaf(v[1].x, v[1].x, v[1].y * v[1].y);
-      if (c != 0.f) {
-        float2 e[2];
-        if (__all_sync(0xffffffffu, cabs * fmaxf(pw0, pw1) <= kKerrTierB)) {
-          const KerrPolyB kb = *reinterpret_cast<const KerrPolyB*>(sh.kerr + i * 8);
-          float2 cs, sn;
-          kerr_pair_b(make_float2(pw0, pw1), kb, cs, sn);
-          e[0] = make_float2(cs.x, sn.x);
-          e[1] = make_float2(cs.y, sn.y);
-        } else {
-          e[0] = expj<true>(c * pw0);
-          e[1] = expj<true>(c * pw1);
-        }
-#pragma unroll
-        for (int d = 0; d < 2; ++d) {
-          const float2 w = cmul(e[d], v[d]);
-          const float im = fmaf(w.y, g[r + d].x, -w.x * g[r + d].y);  // Im(w conj(g))
-          const float2 ge = cmulc(g[r + d], e[d]);                      // g conj(e)
-          const float k2 = -2.f * c * im;
-          g[r + d] = make_float2(fmaf(k2, v[d].x, ge.x), fmaf(k2, v[d].y, ge.y));
-          if (r + d >= lo && r + d < hi) accc = fmaf(-(d ? pw1 : pw0), im, accc);
-        }
-      } else {
-#pragma unroll
-        for (int d = 0; d < 2; ++d) {
-          const float im = fmaf(v[d].y, g[r + d].x, -v[d].x * g[r + d].y);
-          if (r + d >= lo && r + d < hi) accc = fmaf(-(d ? pw1 : pw0), im, accc);
-        }
-      }
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        if (r + d >= lo && r + d < hi) {
-          const float2 g1 = g[r + d], g2 = make_float2(g1.y, g1.x);
-          P[0] = __ffma2_rn(g1, xe[K + r + d], P[0]);
-          Q[0] = __ffma2_rn(g2, xe[K + r + d], Q[0]);
-#pragma unroll
-          for (int k = 1; k <= K; ++k) {
-            const float2 sk = __fadd2_rn(xe[K + r + d - k], xe[K + r + d + k]);
-            P[k] = __ffma2_rn(g1, sk, P[k]);
-            Q[k] = __ffma2_rn(g2, sk, Q[k]);
-          }
-        }
+    const float4* h4 = sh.taps + i * (KC + 1);
+    const KerrPolyB* kpoly = reinterpret_cast<const KerrPolyB*>(sh.kerr + i * 8);
+    bool& bj = bulk[j];
+#define LDBP_FIX_STEP(k) fix_step<k, KC>(p, i, tile, h4, kpoly, g, sh, parity, lo, hi, lane, warp, tid, b, g0, bj)
+    if constexpr (KFIX >= 0) {
+      LDBP_FIX_STEP(KFIX);
+    } else {
+      switch (p.K[i]) {
+        case 0: LDBP_FIX_STEP(0); break;
+        case 1: LDBP_FIX_STEP(1); break;
+        case 2: LDBP_FIX_STEP(2); break;
+        case 3:
+          if constexpr (KC >= 3) LDBP_FIX_STEP(3);
+          break;
+        case 4:
+          if constexpr (KC >= 4) LDBP_FIX_STEP(4);
+          break;
+        default: break;
       }
     }
-    float2 acc[K + 1];
-#pragma unroll
-    for (int k = 0; k <= K; ++k) acc[k] = make_float2(P[k].x + P[k].y, Q[k].x - Q[k].y);
-#pragma unroll
-    for (int k = 0; k <= K; ++k) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        acc[k].x += __shfl_xor_sync(0xffffffffu, acc[k].x, o);
-        acc[k].y += __shfl_xor_sync(0xffffffffu, acc[k].y, o);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) accc += __shfl_xor_sync(0xffffffffu, accc, o);
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k <= K; ++k) sh.red[warp * (K + 2) + k] = acc[k];
-      sh.red[warp * (K + 2) + K + 1] = make_float2(accc, 0.f);
-    }
-    __syncthreads();
-    // every thread is done reading this step's tile: refill the buffer
-    if (i >= 2) bulk[j] = fix_issue_load(p, sh, j, i - 2, b, g0);
-    if (tid <= K + 1) {
-      float2 s = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int w = 0; w < kNW; ++w) s = cadd(s, sh.red[w * (K + 2) + tid]);
-      const int slot = tid <= K ? tid : CLS + 1;
-      p.partial[((long long)blockIdx.x * p.M + i) * (CLS + 2) + slot] = s;
-    }
-    // g_u = A^H g_v
-    {
-      float2 ge[kR + 2 * K];
-      float2* ef = sh.edges + parity * 2 * kNW * kFwdEdge;
-      tile_extend<K, kR, kNW>(g, ge, ef, ef + kNW * kFwdEdge, lane, warp);
-      parity ^= 1;
-      tile_fir<K, true, kR>(ge, h4, g);
-    }
+#undef LDBP_FIX_STEP
   }
   if (timed_out) {
     // let in-flight copies land before the block's shared memory is released
@@ -291,11 +324,10 @@ __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_const
   }
 }
 
-template <int K>
+template <int KC, int KFIX>
 cudaError_t launch_fix(const BwdParams& p, int grid, cudaStream_t st) {
-  constexpr int CLS = K <= 2 ? 2 : (K <= 4 ? 4 : (K <= 8 ? 8 : 16));
-  const size_t smem = fix_smem_bytes<K>(p.M);
-  auto kern = ldbp_bwd_fix_kernel<K, CLS>;
+  const size_t smem = fix_smem_bytes<KC>(p.M);
+  auto kern = ldbp_bwd_fix_kernel<KC, KFIX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, kNT, smem, st>>>(p);
@@ -305,18 +337,26 @@ cudaError_t launch_fix(const BwdParams& p, int grid, cudaStream_t st) {
 }  // namespace
 
 int bwd_fixed_width(const BwdParams& p) {
-  for (int i = 1; i < p.M; ++i)
-    if (p.K[i] != p.K[0]) return -1;
-  return p.K[0] >= 1 && p.K[0] <= 4 ? p.K[0] : -1;
+  int kmax = 0;
+  bool uniform = true;
+  for (int i = 0; i < p.M; ++i) {
+    kmax = p.K[i] > kmax ? p.K[i] : kmax;
+    uniform = uniform && p.K[i] == p.K[0];
+  }
+  if (kmax > 4) return -1;
+  if (uniform) return p.K[0] >= 1 ? p.K[0] : -1;
+  return kFixMixed + (kmax <= 2 ? 2 : 4);
 }
 
-cudaError_t launch_ldbp_bwd_fixed(const BwdParams& p, int K, cudaStream_t st) {
+cudaError_t launch_ldbp_bwd_fixed(const BwdParams& p, int sel, cudaStream_t st) {
   const int grid = p.batch * p.tiles_per_wave;
-  switch (K) {
-    case 1: return launch_fix<1>(p, grid, st);
-    case 2: return launch_fix<2>(p, grid, st);
-    case 3: return launch_fix<3>(p, grid, st);
-    case 4: return launch_fix<4>(p, grid, st);
+  switch (sel) {
+    case 1: return launch_fix<2, 1>(p, grid, st);
+    case 2: return launch_fix<2, 2>(p, grid, st);
+    case 3: return launch_fix<4, 3>(p, grid, st);
+    case 4: return launch_fix<4, 4>(p, grid, st);
+    case kFixMixed + 2: return launch_fix<2, -1>(p, grid, st);
+    case kFixMixed + 4: return launch_fix<4, -1>(p, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -72,6 +72,8 @@ def _check(Ts, B, n, pw, seed, tol=1e-4):
     ([5] * 25, 2, 10000),
     ([7] * 25, 3, 16384),
     ([5, 3] * 12 + [5], 2, 9000),
+    ([9, 7] * 12 + [9], 2, 10000),
+    ([9, 1, 7, 5, 3] * 5, 2, 8192),
     ([9] * 25, 1, 16384),
     ([15] * 25, 1, 12000),
     ([31] * 25, 1, 12000),
