@@ -367,10 +367,16 @@ typedef struct {
  *  n             a power of two in 512..131072, or three times a power of two
  *                in 1536..49152 (the 6 samples/symbol grids of the analog-rate
  *                simulation: clusters of 3, 6 or 12 blocks).
- * One kernel launch runs all steps; each waveform stays in the shared memory
- * of a thread-block cluster.  The first call for a given (device, fiber,
- * link, fs, n) computes the FP64 spectral tables and uploads them into
- * library-owned device memory (cudaMalloc + synchronous copy); later calls
+ * Execution: for most lengths and batches one kernel launch runs all steps,
+ * each waveform held in the shared memory of a thread-block cluster.
+ * Batches of 24 or more waveforms of n = 65536 and of 8 or more of n = 131072
+ * run instead as two kernels per step (row and column transforms of the
+ * n = N1 x 256 four-step split), in chunks of at most 64 MB of samples that
+ * stay in the L2 cache across the steps.  Both give the same results to FP32
+ * rounding.  The first call for a given (device, fiber, link, fs, n)
+ * computes the FP64 spectral tables and uploads them into library-owned
+ * device memory (cudaMalloc + synchronous copy), and the first run on the
+ * two-kernel path adds transposed copies and twiddle tables; later calls
  * reuse them.
  * Errors: LDBP_EINVAL (NULL pointer, n not a supported length,
  * non-positive fs/span/steps/batch, negative alpha); LDBP_ENONFINITE (a NaN
