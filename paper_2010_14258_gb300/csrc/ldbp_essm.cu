@@ -473,10 +473,17 @@ int ldbp_essm_backward(const void* taps, int32_t taps_stride, const int32_t* T, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   float2* gt = static_cast<float2*>(gtaps);
   cudaError_t e;
+  // filter classes: kappa <= 8, exactly 17..20 (the paper's kappa = 20 without
+  // padding: smaller windows and fewer sums in registers), else <= 24
+  const bool k20 = kapmax >= 17 && kapmax <= 20;
   if (kmax <= 4)
-    e = kapmax <= 8 ? essm_bwd_launch<4, 8>(p, grid, gt, geta, st) : essm_bwd_launch<4, 24>(p, grid, gt, geta, st);
+    e = kapmax <= 8 ? essm_bwd_launch<4, 8>(p, grid, gt, geta, st)
+        : k20       ? essm_bwd_launch<4, 20>(p, grid, gt, geta, st)
+                    : essm_bwd_launch<4, 24>(p, grid, gt, geta, st);
   else
-    e = kapmax <= 8 ? essm_bwd_launch<8, 8>(p, grid, gt, geta, st) : essm_bwd_launch<8, 24>(p, grid, gt, geta, st);
+    e = kapmax <= 8 ? essm_bwd_launch<8, 8>(p, grid, gt, geta, st)
+        : k20       ? essm_bwd_launch<8, 20>(p, grid, gt, geta, st)
+                    : essm_bwd_launch<8, 24>(p, grid, gt, geta, st);
   if (e != cudaSuccess) return cuda_fail(e, "ldbp_essm_backward launch");
   return LDBP_OK;
 }

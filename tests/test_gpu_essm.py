@@ -86,6 +86,9 @@ def _eta_dev(etas):
     ([9] * 8, [6] * 8, 2, 9000),
     ([5, 3, 1, 7], [20, 0, 3, 8], 1, 8192),
     ([3, 3], [2, 1], 2, 1001),
+    ([9] * 4, [17, 20, 18, 19], 2, 8192),   # the exact kappa 17..20 filter class
+    ([17, 9], [20, 5], 1, 8192),            # the same class with the wider FIR class
+    ([9, 3], [17, 24], 1, 6000),            # the kappa <= 24 class
 ])
 def test_essm_backward_parity(Ts, kappas, B, n):
     import torch
