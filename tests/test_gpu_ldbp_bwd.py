@@ -163,6 +163,11 @@ def test_training_shape_pruned_sampled():
     _check([7] * 25, 3, 32768, 2e-3, seed=78)
 
 
+def test_training_shape_alternating_sampled():
+    # the same shape with the alternating 5/3 targets of Sec. V-B (mixed widths)
+    _check([5, 3] * 12 + [5], 3, 32768, 2e-3, seed=79)
+
+
 @pytest.mark.parametrize("Ts,B,n", [([9] * 25, 2, 12000), ([7] * 25, 2, 12001), ([5, 3] * 6 + [1], 2, 9001)])
 def test_backward_c_gradients_match_oracle(Ts, B, n):
     # Remark 1: gradients of the nonlinear coefficients (learnable scaling);

@@ -137,6 +137,24 @@ def test_full_size_dbp_sampled():
         assert rel_l2(to_np(y[b]), ref) <= 1e-4
 
 
+def test_full_size_dbp_sampled_131072():
+    # 128 x 131072, 25 x 80 km, 1 StPS asymmetric DBP on the L2-resident path
+    # (two 64 MB chunks): waveforms of both chunks vs the oracle
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    fs = 20e9
+    fib = synth.Fiber()
+    link = synth.Link(25, 80.0, 1, False, False)
+    g = torch.Generator(device="cuda").manual_seed(4)
+    x = torch.randn(128, 131072, generator=g, device="cuda", dtype=torch.complex64) * (1e-3 ** 0.5)
+    y = api.dbp_apply(fib, link, fs, x, steps_per_span=1, symmetric=False)
+    torch.cuda.synchronize()
+    for b in (0, 63, 64, 127):
+        ref = nlse.dbp(to_np(x[b]), fib, link, fs, steps_per_span=1, symmetric=False)
+        assert rel_l2(to_np(y[b]), ref) <= 1e-4, b
+
+
 @pytest.mark.parametrize("B,n,fs,spans,span_km,stps,sps", [
     (64, 32768, 20e9, 25, 80.0, 100, 2),    # the training channel: 25 x 80 km, 100 StPS, ASE
     (128, 131072, 128e9, 10, 100.0, 200, 4),  # 32 GBd at 4 samples/symbol, 10 x 100 km, 200 StPS, ASE
