@@ -29,10 +29,11 @@ struct TapReduceK {
 };
 
 cudaError_t launch_ldbp_bwd(const BwdParams& p, int kmax_class, cudaStream_t st);
-// Models with every K_i <= 4 run ldbp_bwd_fix_kernel (ldbp_bwd_fix.cu):
-// bwd_fixed_width returns the instance to launch (K for one width 1..4 in
-// every step, kFixMixed + class for mixed widths of class 2 or 4), else -1.
-constexpr int kFixMixed = 100;
+// ldbp_bwd_fix_kernel (ldbp_bwd_fix.cu) runs every model except the mixed
+// ones with a filter wider than T = 17: bwd_fixed_width returns the instance
+// to launch (class * kFixSel + K for one width K in every step, class *
+// kFixSel + kFixMixed for mixed widths), else -1 (ldbp_bwd_kernel).
+constexpr int kFixSel = 32, kFixMixed = 31;
 int bwd_fixed_width(const BwdParams& p);
 cudaError_t launch_ldbp_bwd_fixed(const BwdParams& p, int sel, cudaStream_t st);
 cudaError_t launch_tap_reduce(const float2* partial, int tiles, int M, int pstride, const TapReduceK& kk,

@@ -1,5 +1,5 @@
-// Learned-DBP adjoint for models whose filters have half-widths K_i <= 4
-// (T_i <= 9; one width in every step, or mixed): the same reverse sweep and the same per-block
+// Learned-DBP adjoint for every model except mixed-width ones with a filter
+// wider than T = 17 (those run ldbp_bwd_kernel): the same reverse sweep and the same per-block
 // partial sums as ldbp_bwd_kernel (Eq. (7), Sec. III-B; the Kerr and FIR
 // adjoints and the tap and c gradients are stated there), computed in a
 // layout that fits two 256-thread blocks per SM:
@@ -32,7 +32,6 @@ constexpr int kR = kFwdR;            // 16 consecutive samples per thread
 constexpr int kNT = kFwdNT;          // 256 threads
 constexpr int kNW = kNT / 32;
 constexpr int kS = kR * kNT;         // 4096-sample tile
-constexpr int kNQ = kR / 2;          // float4 chunks per thread
 
 struct FixShared {
   float2* ubuf;    // [2][kS] checkpoints (TMA destination, linear)
@@ -225,10 +224,11 @@ __device__ __forceinline__ void fix_step(const BwdParams& p, int i, const float2
   tile_fir<K, true, kR>(ge, h4, g);
 }
 
-// KFIX >= 0: every step has half-width KFIX (= KC); KFIX < 0: per-step
-// dispatch over the half-widths 0..KC (uniform per block).
+// KFIX >= 0: every step has half-width KFIX; KFIX < 0: per-step dispatch over
+// the half-widths 0..KC (uniform per block; KC <= 8).  Two blocks per SM for
+// the classes up to K = 4 (128 registers), one for the wider ones.
 template <int KC, int KFIX>
-__global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_constant__ BwdParams p) {
+__global__ void __launch_bounds__(kNT, (KC <= 4 ? 2 : 1)) ldbp_bwd_fix_kernel(const __grid_constant__ BwdParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   FixShared sh;
   sh.ubuf = reinterpret_cast<float2*>(smem_raw);
@@ -305,6 +305,9 @@ __global__ void __launch_bounds__(kNT, 2) ldbp_bwd_fix_kernel(const __grid_const
         case 4:
           if constexpr (KC >= 4) LDBP_FIX_STEP(4);
           break;
+#define LDBP_FIX_CASE(k) case k: if constexpr (KC >= k) LDBP_FIX_STEP(k); break;
+        LDBP_FIX_CASE(5) LDBP_FIX_CASE(6) LDBP_FIX_CASE(7) LDBP_FIX_CASE(8)
+#undef LDBP_FIX_CASE
         default: break;
       }
     }
@@ -343,20 +346,32 @@ int bwd_fixed_width(const BwdParams& p) {
     kmax = p.K[i] > kmax ? p.K[i] : kmax;
     uniform = uniform && p.K[i] == p.K[0];
   }
-  if (kmax > 4) return -1;
-  if (uniform) return p.K[0] >= 1 ? p.K[0] : -1;
-  return kFixMixed + (kmax <= 2 ? 2 : 4);
+  if (uniform && kmax == 0) return -1;
+  const int cls = kmax <= 2 ? 2 : kmax <= 4 ? 4 : kmax <= 8 ? 8 : 16;
+  // mixed widths beyond K = 8: the switch over 17 step instances spills
+  // heavily at one block per SM; ldbp_bwd_kernel handles those
+  if (!uniform && cls == 16) return -1;
+  return cls * kFixSel + (uniform ? kmax : kFixMixed);
 }
 
 cudaError_t launch_ldbp_bwd_fixed(const BwdParams& p, int sel, cudaStream_t st) {
   const int grid = p.batch * p.tiles_per_wave;
-  switch (sel) {
-    case 1: return launch_fix<2, 1>(p, grid, st);
-    case 2: return launch_fix<2, 2>(p, grid, st);
-    case 3: return launch_fix<4, 3>(p, grid, st);
-    case 4: return launch_fix<4, 4>(p, grid, st);
-    case kFixMixed + 2: return launch_fix<2, -1>(p, grid, st);
-    case kFixMixed + 4: return launch_fix<4, -1>(p, grid, st);
+  const int cls = sel / kFixSel, k = sel % kFixSel;
+  if (k == kFixMixed) {
+    switch (cls) {
+      case 2: return launch_fix<2, -1>(p, grid, st);
+      case 4: return launch_fix<4, -1>(p, grid, st);
+      case 8: return launch_fix<8, -1>(p, grid, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (k) {
+#define LDBP_FIX_LAUNCH(kk, cc) case kk: return launch_fix<cc, kk>(p, grid, st);
+    LDBP_FIX_LAUNCH(1, 2) LDBP_FIX_LAUNCH(2, 2) LDBP_FIX_LAUNCH(3, 4) LDBP_FIX_LAUNCH(4, 4)
+    LDBP_FIX_LAUNCH(5, 8) LDBP_FIX_LAUNCH(6, 8) LDBP_FIX_LAUNCH(7, 8) LDBP_FIX_LAUNCH(8, 8)
+    LDBP_FIX_LAUNCH(9, 16) LDBP_FIX_LAUNCH(10, 16) LDBP_FIX_LAUNCH(11, 16) LDBP_FIX_LAUNCH(12, 16)
+    LDBP_FIX_LAUNCH(13, 16) LDBP_FIX_LAUNCH(14, 16) LDBP_FIX_LAUNCH(15, 16) LDBP_FIX_LAUNCH(16, 16)
+#undef LDBP_FIX_LAUNCH
     default: return cudaErrorInvalidValue;
   }
 }

@@ -74,6 +74,9 @@ def _check(Ts, B, n, pw, seed, tol=1e-4):
     ([5, 3] * 12 + [5], 2, 9000),
     ([9, 7] * 12 + [9], 2, 10000),
     ([9, 1, 7, 5, 3] * 5, 2, 8192),
+    ([15, 13, 9, 1] * 6 + [15], 2, 8192),
+    ([21] * 10, 1, 9000),
+    ([33] * 3, 1, 7000),
     ([9] * 25, 1, 16384),
     ([15] * 25, 1, 12000),
     ([31] * 25, 1, 12000),
