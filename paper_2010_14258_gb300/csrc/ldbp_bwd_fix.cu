@@ -1,10 +1,11 @@
 // Learned-DBP adjoint for every model except mixed-width ones with a filter
-// wider than T = 17 (those run ldbp_bwd_kernel): the same reverse sweep and the same per-block
-// partial sums as ldbp_bwd_kernel (Eq. (7), Sec. III-B; the Kerr and FIR
-// adjoints and the tap and c gradients are stated there), computed in a
-// layout that fits two 256-thread blocks per SM:
+// wider than T = 17 (those run ldbp_bwd_kernel): the same reverse sweep and
+// the same per-block partial sums as ldbp_bwd_kernel (Eq. (7), Sec. III-B; the
+// Kerr and FIR adjoints and the tap and c gradients are stated there),
+// computed in a layout that fits two 256-thread blocks per SM up to K = 4
+// (one block for the wider classes):
 //  * K is a compile-time constant of the step (one instance for a uniform
-//    model; a per-step switch over K = 0..4 otherwise);
+//    model; a per-step switch over K = 0..8 otherwise);
 //  * one pass over sample pairs recomputes the forward FIR output v, applies
 //    the Kerr adjoint in place over the incoming gradient and accumulates the
 //    tap-gradient products, so v is never held for all samples: the rotation
