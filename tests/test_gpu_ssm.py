@@ -257,3 +257,26 @@ def test_l2_path_agrees_with_cluster_kernel(n, B):
     a = _dbp(x[:4], fib, link, fs, 1, False)
     b = _dbp(x, fib, link, fs, 1, False)
     assert rel_l2(b[:4], a) <= 1e-5
+
+
+@pytest.mark.parametrize("n,B", [(4096, 3), (65536, 24), (131072, 8)])
+def test_in_place_equals_out_of_place(n, B):
+    # y == x is allowed for ssm_forward and dbp_apply, on the cluster kernel
+    # (n = 4096) and on the L2-resident path; the same kernels run either way,
+    # so the results are bitwise equal
+    import torch
+    from paper_2010_14258_gb300 import api
+    gpu_lib()
+    fs = 20e9
+    fib = synth.Fiber()
+    ch = synth.Link(2, 80.0, 2, True, True, 5.0, 1.946e14, seed=31, counter=2)
+    x = to_dev(_sig(B, n, 101, 2e-3))
+    ref = api.ssm_forward(fib, ch, fs, x.clone())
+    xi = x.clone()
+    api.ssm_forward(fib, ch, fs, xi, out=xi)
+    dref = api.dbp_apply(fib, ch, fs, ref, steps_per_span=2, symmetric=True)
+    di = ref.clone()
+    api.dbp_apply(fib, ch, fs, di, steps_per_span=2, symmetric=True, out=di)
+    torch.cuda.synchronize()
+    assert torch.equal(xi, ref)
+    assert torch.equal(di, dref)
