@@ -87,7 +87,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=B, help="waveforms per GPU (profiling runs use fewer)")
     ap.add_argument("--profile", default="", choices=["", "ldbp", "dbp", "dbp_cufft", "ldbp_bwd", "channel",
-                                                      "resample", "analog_channel", "train_channel", "long_channel"],
+                                                      "resample", "analog_channel", "train_channel", "long_channel",
+                                                      "essm", "essm_bwd"],
                     help="run only this kernel (warmup + steps launches) on random input, for ncu captures")
     ap.add_argument("--workload", default="ldbp",
                     choices=["ldbp", "channel", "ragged", "train", "train_prune", "sym32", "essm", "analog"],
@@ -346,6 +347,23 @@ def profile_only(args, api):
         units = B * 32768 * M_STEPS * 4
         n_wave = 32768
         fn = lambda: api.ssm_forward(fib, ch, FS, xt, out=yt)  # noqa: E731
+    elif args.profile in ("essm", "essm_bwd"):
+        # the learned enhanced SSM on --batch waveforms: T = --taps (default 9), a
+        # unit (2 kappa + 1)-tap filter with kappa = 20 in every step
+        kap = 20
+        T = args.taps or 9
+        taps_np, c = ls_model(T)
+        taps = pack_taps(taps_np)
+        e = np.zeros((M_STEPS, 2 * kap + 1), np.float32)
+        e[:, kap] = 1.0
+        ed = torch.from_numpy(e).cuda()
+        ks = [kap] * M_STEPS
+        if args.profile == "essm":
+            fn = lambda: api.ldbp_essm_apply(taps, [T] * M_STEPS, c, ed, ks, nxt(), out=y)  # noqa: E731
+        else:
+            ck = torch.empty((M_STEPS, B, N_SAMP), dtype=torch.complex64, device="cuda")
+            api.ldbp_essm_apply(taps, [T] * M_STEPS, c, ed, ks, x, ckpt=ck, out=y)
+            fn = lambda: api.ldbp_essm_backward(taps, [T] * M_STEPS, c, ed, ks, ck, x)  # noqa: E731
     elif args.profile == "long_channel":
         # the data-generation channel's shape: --batch frames of 131072 samples,
         # 10 x 100 km, 200 symmetric StPS with ASE (the L2-resident path from 8 frames)
